@@ -1,0 +1,158 @@
+/*
+ * pdg_oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, serial, FP64 CPU restatement of the method of arXiv 2404.18034
+ * (6-DoF powered-descent guidance solved by prox-linear SCP with the CTCS
+ * reformulation and a customized PIPG subproblem solver).  It exists to check
+ * the CUDA solver; only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load it.  It shares no code, header or constant
+ * table with the CUDA path: its parameter struct below is its own.
+ *
+ * Every routine follows a passage of the paper, cited as "Sec.", "Eq." or
+ * "Alg." in the implementation.  Readings of silent or garbled passages are
+ * listed next to the code that takes them.
+ *
+ * Layouts (row-major, double):
+ *   state  x[15]  = (m, r[3], v[3], q[4], omega[3], y)      (Sec. 2.1, Sec. 5)
+ *   control u[nu] = (T[3], [gamma[3],] s), nu in {4, 7}     (Sec. 2.1, Sec. 5)
+ *   X[N][15], U[N][nu]; A[N-1][15][15]; Bm, Bp[N-1][15][nu]; xprop[N-1][15]
+ */
+#ifndef PDG_ORACLE_H
+#define PDG_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_NX 15
+#define ORC_NU_MAX 7
+
+typedef struct orc_params {
+  int nu;                 /* 4: (T, s); 7: (T, gamma, s) */
+  double alpha_mdot;      /* mass depletion per unit thrust */
+  double g_I[3];          /* gravity, inertial frame */
+  double J_B[3];          /* diagonal inertia */
+  double r_T_B[3];        /* thrust point, body frame */
+  double m_dry, v_max, theta_max, omega_max, delta_max, T_min, T_max, gamma_max;
+  double s_min, s_max;    /* dilation box */
+  double z_f[15];         /* final-state targets (index as x) */
+  int fix_f[15];          /* 1 where the final state component is fixed */
+  double P_x[15], P_u[7]; /* diagonal scalings */
+  double w_cost, w_prox, w_ep, eps_ctcs;
+  double pipg_omega, pipg_rho, pipg_eps_abs, pipg_eps_rel;
+  int pipg_jmax, pipg_jcheck;
+  double pow_eps_abs, pow_eps_rel, pow_eps_buff;
+  int pow_jmax;
+  int scp_jmax;
+  double scp_eps_step, scp_eps_defect;
+  int rk4_substeps;
+  double tf_guess;        /* initial guess of the final time */
+} orc_params;
+
+/* Scaled convex subproblem data (Eq. cvx-subproblem-custom). */
+typedef struct orc_qp {
+  int N, nu;
+  double *Am;   /* [N-1][15][15]  hat A^-_k */
+  double *Ap;   /* [N-1][15][15]  hat A^+_k = -I */
+  double *Bm;   /* [N-1][15][nu]  hat B^-_k */
+  double *Bp;   /* [N-1][15][nu]  hat B^+_k */
+  double *w;    /* [N-1][15]      hat w_k */
+  double *eps;  /* [N-1]          hat epsilon_k */
+  double *umin; /* [N][nu]        hat u_{k,min} (-inf where unbounded) */
+  double *umax; /* [N][nu]        hat u_{k,max} (+inf where unbounded) */
+  double zi[15];
+  double zf[15];
+  int fixf[15];
+  double w_cost, w_prox, w_ep;
+  double ecost[15]; /* e_cost on the scaled x_N (Sec. 4 objective) */
+} orc_qp;
+
+/* PIPG primal-dual state (warm start in, solution out), Alg. PIPG_custom. */
+typedef struct orc_pd {
+  double *xh;   /* [N][15] */
+  double *uh;   /* [N][nu] */
+  double *mup;  /* [N-1][15] */
+  double *mum;  /* [N-1][15] */
+  double *phi;  /* [N-1][15] */
+  double *th;   /* [N-1] */
+} orc_pd;
+
+/* ---- model (Sec. 5) ---- */
+void orc_F(const orc_params* p, const double* x, const double* u, double* Fx);   /* dxi/dt, 14 */
+int  orc_g(const orc_params* p, const double* x, const double* u, double* g);    /* returns n_g */
+void orc_f(const orc_params* p, const double* x, const double* u, double* f);    /* Eq. sys-dyn-dil-aug, 15 */
+void orc_jac(const orc_params* p, const double* x, const double* u, double* A, double* B);
+
+/* ---- discretization (Sec. 3.2, Sec. 3.3.1) ---- */
+void orc_flow(const orc_params* p, const double* xk, const double* uk, const double* uk1,
+              int nsub, double* xout);
+void orc_discretize(const orc_params* p, int N, const double* X, const double* U,
+                    double* A, double* Bm, double* Bp, double* xprop);
+
+/* ---- scaled subproblem (Sec. 3.3.2) ---- */
+int  orc_qp_alloc(orc_qp* qp, int N, int nu);
+void orc_qp_free(orc_qp* qp);
+void orc_scale(const orc_params* p, int N, const double* x0, const double* X, const double* U,
+               const double* A, const double* Bm, const double* Bp, const double* xprop, orc_qp* qp);
+
+int  orc_pd_alloc(orc_pd* s, int N, int nu);
+void orc_pd_free(orc_pd* s);
+void orc_pd_zero(orc_pd* s, int N, int nu);
+void orc_pd_copy(orc_pd* dst, const orc_pd* src, int N, int nu);
+
+/* ---- solver (Sec. 4) ---- */
+/* Alg. power.  force_iters > 0 runs exactly that many iterations. Returns sigma. */
+double orc_power(const orc_params* p, const orc_qp* qp, const orc_pd* start, int force_iters, int* iters);
+/* Alg. PIPG_custom + Alg. stopping.  ws is warm start in / solution out.
+ * force_iters > 0 runs exactly that many iterations without the stop test.
+ * Returns the number of iterations run. */
+int orc_pipgc(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, int force_iters);
+
+/* Dense canonical QP (Eq. canonical-QP / parsed-data) and generic PIPG (Alg. 1). */
+int  orc_qp_dim(int N, int nu);  /* n_z */
+void orc_qp_dense(const orc_qp* qp, double* P, double* pv, double* G, double* gv,
+                  double* H, double* hv, double* lo, double* hi);
+void orc_pipg_generic(const orc_qp* qp, double alpha, double omega, double rho, int jmax,
+                      const double* z1, const double* eta1, const double* chi1,
+                      double* zout, double* wout, double* vout);
+void orc_z_pack(const orc_qp* qp, const orc_pd* s, double* z);
+void orc_z_unpack(const orc_qp* qp, const double* z, orc_pd* s);
+
+/* Jacobi eigenvalues of a dense symmetric matrix (in place; returns the largest). */
+double orc_sym_eig_max(int n, double* M);
+
+/* ---- SCP (Sec. 3.3) ---- */
+void orc_init_guess(const orc_params* p, int N, const double* x0, double* X, double* U);
+
+typedef struct orc_result {
+  double tf, fuel;
+  int status;          /* 0 converged, 1 max SCP iterations, 2 non-finite */
+  int scp_iters;
+  long long pipg_iters;
+  long long pow_iters;
+  double defect, step;  /* last convergence measures */
+} orc_result;
+
+/* One SCP iteration about (X, U): discretize, scale, power iteration, PIPG.
+ * ws: warm start in / subproblem solution out.  Outputs the subproblem data
+ * measures and counts.  force_pipg / force_pow > 0 replay given counts. */
+int orc_scp_iterate(const orc_params* p, int N, const double* x0, double* X, double* U,
+                    orc_pd* ws, int force_pow, int force_pipg,
+                    double* sigma, int* pow_it, int* pipg_it, double* defect, double* step);
+
+/* Full solve.  trace (may be NULL) is [scp_jmax][2] = (power iters, PIPG iters)
+ * per SCP iteration, written on output; when replay != 0 it is read instead and
+ * forces those counts, and replay_scp forces the SCP iteration count. */
+int orc_solve(const orc_params* p, int N, const double* x0, double* X, double* U,
+              orc_result* res, int* trace, int replay, int replay_scp);
+
+/* Batch over instances with OpenMP (nthreads <= 0: library default).
+ * X: [B][Nmax][15], U: [B][Nmax][nu]; N may differ per instance. */
+int orc_solve_batch(const orc_params* p, int B, int Nmax, const int* Ns, const double* x0s,
+                    double* X, double* U, double* tf, double* fuel, int* status,
+                    int* scp_iters, long long* pipg_iters, int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

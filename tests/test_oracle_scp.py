@@ -1,0 +1,89 @@
+"""Pins of the oracle's full SCP solve (Sec. 2.3, Sec. 7): a converged
+trajectory satisfies the nonlinear dynamics on re-propagation, the CTCS
+budget and the path constraints between nodes; replaying recorded counts
+reproduces a solve; the paper's Monte Carlo distribution converges."""
+import numpy as np
+import pytest
+
+
+def _fine_defects(O, p, X, U, nsub=200):
+    N = X.shape[0]
+    out = []
+    for k in range(N - 1):
+        uk, uk1 = U[k].copy(), U[k + 1].copy()
+        uk[-1] /= (N - 1); uk1[-1] /= (N - 1)
+        out.append(np.abs(O.flow(p, X[k], uk, uk1, nsub) - X[k + 1]) / p["P_x"])
+    return np.array(out)
+
+
+def _dense_g(O, p, X, U, nsamp=40):
+    N, nu = U.shape
+    gs = []
+    for k in range(N - 1):
+        x = X[k].copy()
+        uk, uk1 = U[k].copy(), U[k + 1].copy()
+        for i in range(nsamp):
+            lp = i / nsamp
+            u = (1 - lp) * U[k] + lp * U[k + 1]
+            gs.append(O.g(p, x, u))
+            a = uk * (1 - lp) + uk1 * lp
+            b = uk * (1 - lp - 1 / nsamp) + uk1 * (lp + 1 / nsamp)
+            a[-1] /= (N - 1) * nsamp; b[-1] /= (N - 1) * nsamp
+            x = O.flow(p, x, a, b, 20)
+    return np.array(gs)
+
+
+@pytest.mark.parametrize("nu", [4, 7])
+def test_converged_solution_is_feasible(oracle, inputs, nu):
+    p = inputs.load_params(nu=nu)
+    N = 15
+    x0 = inputs.dispersion(p, 1, 21, "bj")[0]
+    r = oracle.solve(p, N, x0)
+    assert r["status"] == 0, r
+    X, U = r["X"], r["U"]
+    assert r["defect"] <= p["scp_eps_defect"] and r["step"] <= p["scp_eps_step"]
+    np.testing.assert_allclose(X[0, :14], x0, atol=1e-12)
+    assert X[0, 14] == 0.0
+    fx = p["fix_f"].astype(bool)
+    np.testing.assert_allclose(X[-1][fx], p["z_f"][fx], atol=1e-9)
+    d = _fine_defects(oracle, p, X, U)
+    assert d[:, :14].max() < 2e-3, d.max()
+    assert X[-1, 14] - X[0, 14] <= (N - 1) * p["eps_ctcs"] + 1e-9
+    np.testing.assert_allclose(np.linalg.norm(X[:, 7:11], axis=1), 1.0, atol=5e-3)
+    assert np.all(np.diff(X[:, 0]) <= 1e-6)
+    g = _dense_g(oracle, p, X, U)
+    assert np.maximum(g, 0).max() < 0.05
+    assert np.all(U[:, -1] >= p["s_min"] - 1e-9) and np.all(U[:, -1] <= p["s_max"] + 1e-9)
+    tf = np.sum(0.5 * (U[:-1, -1] + U[1:, -1])) / (N - 1)
+    assert abs(tf - r["tf"]) < 1e-12
+    assert abs((X[0, 0] - X[-1, 0]) - r["fuel"]) < 1e-12
+
+
+def test_replay_reproduces_free_run(oracle, params):
+    x0 = params["x0_nominal"]
+    r = oracle.solve(params, 10, x0)
+    rr = oracle.solve(params, 10, x0, trace=r["trace"], replay_scp=r["scp_iters"])
+    np.testing.assert_array_equal(r["X"], rr["X"])
+    np.testing.assert_array_equal(r["U"], rr["U"])
+    assert r["status"] == rr["status"]
+
+
+def test_batch_matches_single(oracle, inputs, params):
+    x0 = inputs.dispersion(params, 6, 31, "bj")
+    Ns = np.array([10, 15, 10, 20, 15, 10], np.int32)
+    b = oracle.solve_batch(params, x0, Ns, nthreads=3)
+    for i in range(6):
+        r = oracle.solve(params, int(Ns[i]), x0[i])
+        np.testing.assert_array_equal(b["X"][i, :Ns[i]], r["X"])
+        assert b["status"][i] == r["status"] and b["scp_iters"][i] == r["scp_iters"]
+        assert b["pipg_iters"][i] == r["pipg_iters"]
+
+
+def test_paper_monte_carlo_distribution_converges(oracle, inputs):
+    """Sec. 7: r(0) ~ (U(6,9), U(3,6), U(1,2)), SCP <= 25, 2500 PIPG iterations:
+    every run converges (on this project's parameter set)."""
+    p = inputs.load_params(scp_jmax=25, pipg_jmax=2500)
+    x0 = inputs.dispersion(p, 24, inputs.config_seed(99), "paper256")
+    b = oracle.solve_batch(p, x0, np.full(24, 15, np.int32))
+    assert np.all(b["status"] == 0), b["status"]
+    assert b["scp_iters"].max() <= 25
