@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark: converged 6-DoF powered-descent SCP solves per second on GB300.
+
+One step = one full batched solve (every SCP iteration of every instance:
+RK4 discretization with STMs, prescaling, power iteration, PIPG, update) of
+a batch of seeded synthetic dispersed initial conditions (the "bj"
+dispersion), inputs resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp64|fp32] [--mode persistent|plain]
+                  [--batch B] [--nodes N]
+
+Under torchrun each rank solves its own batch (weak scaling, no collective on
+the data path); the timed region is bracketed by barriers and the max over
+ranks is reported.  --impl reference times the FP64 CPU oracle on the host
+cores (rank 0 only) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged PDG SCP solves/s on 1 GB300, batch 16384, N=15; % FP64/FP32 peak"
+SMS = 152
+MAX_SM_MHZ = 2070.0
+FMA_PER_CLK = {"fp64": 2, "fp32": 128}  # per SM, GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--mode", default="persistent", choices=["persistent", "plain"])
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--nodes", type=int, default=15)
+    ap.add_argument("--dispersion", default="bj")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return f"pdg6dof_{a.dispersion}_B{a.batch}_N{a.nodes}_{a.precision}_{a.mode}"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join("/tmp", f"pdg_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_run(p, x0, N, nthreads):
+    import oracle
+    oracle.build()
+    t = time.perf_counter()
+    r = oracle.solve_batch(p, x0, np.full(x0.shape[0], N, np.int32), nthreads=nthreads)
+    dt = time.perf_counter() - t
+    return int(np.sum(r["status"] == 0)), dt
+
+
+def cpu_baseline(p, a, seed, sample):
+    cores = os.cpu_count() or 1
+    x0 = __import__("paper_2404_18034_gb300.inputs", fromlist=["x"]).dispersion(p, a.batch, seed, a.dispersion)
+    if sample <= 0:
+        conv, dt = cpu_oracle_run(p, x0[:cores * 2], a.nodes, cores)
+        per = dt / (cores * 2)
+        sample = int(min(a.batch, max(cores * 2, round(15.0 / max(per, 1e-6)))))
+    conv, dt = cpu_oracle_run(p, x0[:sample], a.nodes, cores)
+    return {"value": conv / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} of the {a.batch} instances of {workload_name(a)} (FP64 oracle, OpenMP over "
+                      f"instances, {cores} threads, {dt:.1f} s); converged solves / wall time",
+            "converged_in_sample": conv}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2404_18034_gb300 import inputs
+    p = inputs.load_params()
+    seed = inputs.config_seed(2)
+    x0 = inputs.dispersion(p, a.batch, seed, a.dispersion)
+    cores = os.cpu_count() or 1
+    per_step = a.cpu_sample or max(cores * 4, 64)
+    per_step = min(per_step, a.batch)
+    times, convs = [], []
+    for s in range(a.warmup + a.steps):
+        lo = (s * per_step) % max(1, a.batch - per_step + 1)
+        conv, dt = cpu_oracle_run(p, x0[lo:lo + per_step], a.nodes, cores)
+        if s >= a.warmup:
+            times.append(dt)
+            convs.append(conv)
+    value = sum(convs) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(a), "batch": a.batch, "nodes": a.nodes,
+                                            "precision": "fp64", "dispersion": a.dispersion,
+                                            "parallelism": f"dp{a.gpus}"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} instances of {workload_name(a)} per step (FP64 oracle, "
+                                       f"OpenMP over instances, {cores} threads)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_18034_gb300 import build, flops, inputs
+    from paper_2404_18034_gb300.pdg_mc import Solver, probe_fma
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    prec = 0 if a.precision == "fp64" else 1
+    p = inputs.load_params()
+    seed = inputs.config_seed(2) + 1000 * rank
+    x0h = inputs.dispersion(p, a.batch, seed, a.dispersion)
+    x0 = torch.from_numpy(x0h).to(dev)
+    S = Solver(p, a.nodes, prec)
+    mode = 1 if a.mode == "persistent" else 0
+    out = S.alloc_outputs(a.batch, dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def step(trace=False):
+        return S.solve(x0, None, mode=mode, out=out, trace=trace, stream=stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    info = S.launch_info()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    conv_counts = []
+    traces = None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(a.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            o = step(trace=True)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    st = out["status"].cpu().numpy()
+    conv = int(np.sum(st == 0))
+    tr = o["trace"].cpu().numpy()
+    scp = out["scp_iters"].cpu().numpy()
+    pipg = out["pipg_iters"].cpu().numpy()
+    pow_it = tr[:, :, 0].sum(1)
+    total_ms = float(np.sum(ms))
+    stats = torch.tensor([total_ms, conv * a.steps, a.batch * a.steps], dtype=torch.float64, device=dev)
+    if world > 1:
+        t_max = stats[0:1].clone()
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        cnt = stats[1:].clone()
+        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+        stats = torch.cat([t_max, cnt])
+    total_ms_max = float(stats[0])
+    value = float(stats[1]) / (total_ms_max * 1e-3)
+
+    # roofline of the dominant kernel (the persistent solve kernel is the whole step)
+    fl = flops.solve_flops(np.full(a.batch, a.nodes), p["nu"], p["rk4_substeps"], scp, pow_it, pipg)
+    launch_s = float(np.mean(ms)) * 1e-3
+    achieved = fl / launch_s / 1e12
+    clocks = clk.summary()
+    peak_nominal = SMS * FMA_PER_CLK[a.precision] * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    try:
+        probe = probe_fma(prec, stream)
+    except RuntimeError:
+        probe = None
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not a.no_e2e:
+        pin = torch.from_numpy(x0h).pin_memory()
+        x0_pinned = pin.numpy()
+        outs = {k: torch.empty(tuple(v.shape), dtype=v.dtype).pin_memory().numpy() for k, v in out.items()
+                if k != "trace"}
+        S.solve_host(x0_pinned, None, mode=mode, out=outs, stream=stream)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e2e_conv = 0
+        for _ in range(a.steps):
+            r = S.solve_host(x0_pinned, None, mode=mode, out=outs, stream=stream)
+            e2e_conv += int(np.sum(r["status"] == 0))
+        e2e_s = time.perf_counter() - t0
+        es = torch.tensor([e2e_s, e2e_conv], dtype=torch.float64, device=dev)
+        if world > 1:
+            t_max = es[0:1].clone()
+            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+            c = es[1:].clone()
+            dist.all_reduce(c, op=dist.ReduceOp.SUM)
+            es = torch.cat([t_max, c])
+        h2d = x0h.nbytes
+        d2h = sum(v.nbytes for v in outs.values())
+        e2e = {"value": float(es[1]) / float(es[0]), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = cpu_baseline(p, a, inputs.config_seed(2), a.cpu_sample)
+
+    launches = a.steps * (1 if mode == 1 else 1 + 4 * int(scp.max()))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "batch_per_gpu": a.batch, "global_batch": a.batch * world,
+                       "nodes": a.nodes, "nu": p["nu"], "precision": a.precision, "mode": a.mode,
+                       "dispersion": a.dispersion, "parallelism": f"dp{world}",
+                       "l2": "256 MiB buffer written between timed steps",
+                       "threads_per_cta": info["threads"], "ctas_per_sm": info["ctas_per_sm"],
+                       "smem_bytes_per_cta": info["smem_bytes"]},
+            "converged_fraction": conv / a.batch,
+            "all_solves_per_s": float(stats[2]) / (total_ms_max * 1e-3),
+            "mean_scp_iters": float(scp.mean()), "mean_pipg_iters_per_solve": float(pipg.mean()),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
+                         "frac": achieved / peak_nominal, "traffic": None,
+                         "kernel": "k_persistent" if mode == 1 else "whole plain-form step",
+                         "flops_per_launch": fl,
+                         "peak_source": f"derived: {SMS} SMs x {FMA_PER_CLK[a.precision]} "
+                                        f"{a.precision.upper()} FMA/clk x 2 flop x {MAX_SM_MHZ:.0f} MHz",
+                         "probe_tflops": probe,
+                         "frac_of_probe": (achieved / probe) if probe else None},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * pdg_mc.h -- C ABI of the batched GB300 solver for Monte Carlo 6-DoF
+ * powered-descent guidance (arXiv 2404.18034).
+ *
+ * Each instance is a free-final-time 6-DoF landing problem (Sec. 5) solved by
+ * prox-linear sequential convex programming (Sec. 2.3, Eq. cvx-subproblem)
+ * with the CTCS reformulation (Sec. 2.1, Eq. sys-dyn-dil-aug).  Every SCP
+ * iteration discretizes the augmented dynamics with their state-transition
+ * matrices (Sec. 2.3.1), prescales the subproblem (Sec. 2.3.2), estimates the
+ * step size by the customized power iteration (Alg. power) and solves the
+ * subproblem by customized PIPG (Alg. PIPG_custom with Alg. stopping).
+ *
+ * Conventions
+ *   - Layouts are row-major, double precision, instance-major:
+ *       x0[B][14]            (m_wet, r[3], v[3], q[4] scalar first, w[3])
+ *       X[B][n_max][15]      (m, r, v, q, w, y); y is the CTCS integrator
+ *       U[B][n_max][nu]      (T[3], s) for nu = 4; (T[3], gamma[3], s) for nu = 7
+ *     Rows k >= n_nodes[b] of X and U are written as zero.
+ *   - Pointers named "device" must point to device memory of the current
+ *     device; the caller owns every buffer it passes.  The handle owns its
+ *     workspace (allocated by pdg_mc_init and grown on demand).
+ *   - All calls are asynchronous on the given CUDA stream (NULL: the legacy
+ *     default stream) unless stated otherwise.
+ *   - Return 0 on success, a negative PDG_E* code on error; the message is
+ *     available from pdg_mc_last_error.  Per-instance solver outcomes are in
+ *     status[], never in the return code.  Nothing throws across the ABI.
+ *   - precision = 1 computes in FP32 (inputs and outputs stay double).
+ */
+#ifndef PDG_MC_H
+#define PDG_MC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDG_OK 0
+#define PDG_EINVAL (-1)   /* bad argument */
+#define PDG_ENOMEM (-2)   /* device allocation failed */
+#define PDG_ECUDA (-3)    /* CUDA runtime error */
+
+/* per-instance status */
+#define PDG_CONVERGED 0
+#define PDG_MAX_SCP 1     /* SCP iteration cap reached without convergence */
+#define PDG_NONFINITE 2   /* a non-finite value appeared */
+#define PDG_BUDGET 3      /* the device-side wall-clock budget ran out */
+#define PDG_BAD_INPUT 4   /* n_nodes out of range or non-finite x0 */
+
+/* Problem and solver parameters; angles in radians.  Sec. 5 lists the model
+ * quantities, Sec. 2.3.2 the scalings P_x, P_u and Sec. 3 the PIPG inputs. */
+typedef struct pdg_params {
+  int nu;                 /* 4 or 7 */
+  int precision;          /* 0 = FP64, 1 = FP32 */
+  double alpha_mdot;      /* mass depletion per unit thrust magnitude */
+  double g_I[3];          /* gravity (inertial) */
+  double J_B[3];          /* diagonal inertia */
+  double r_T_B[3];        /* thrust point (body) */
+  double m_dry, v_max, theta_max, omega_max, delta_max, T_min, T_max, gamma_max;
+  double s_min, s_max;    /* dilation bounds (the only control box) */
+  double z_f[15];         /* final targets, indexed as x */
+  int fix_f[15];          /* 1 where the final component is fixed (E_f) */
+  double P_x[15], P_u[7]; /* diagonal scalings */
+  double w_cost, w_prox, w_ep, eps_ctcs;
+  double pipg_omega, pipg_rho, pipg_eps_abs, pipg_eps_rel;
+  int pipg_jmax, pipg_jcheck;
+  double pow_eps_abs, pow_eps_rel, pow_eps_buff;
+  int pow_jmax;
+  int scp_jmax;
+  double scp_eps_step, scp_eps_defect;
+  int rk4_substeps;
+  double tf_guess;        /* dilation of the initial guess */
+  double budget_seconds;  /* device wall-clock cap per instance; 0 = none */
+} pdg_params;
+
+typedef struct pdg_handle pdg_handle;
+
+/* Create a solver for instances of at most n_max nodes (2 <= n_max <= 32)
+ * on the current device.  Copies *p; validates it (PDG_EINVAL on nonsense).
+ * Allocates nothing large; workspaces grow on first use. */
+int pdg_mc_init(const pdg_params* p, int n_max, pdg_handle** out);
+
+/* Release the handle and its device workspace (synchronizes the device). */
+void pdg_mc_destroy(pdg_handle* h);
+
+/* Last error message of this handle ("" if none).  With h == NULL, the last
+ * error of pdg_mc_init. */
+const char* pdg_mc_last_error(const pdg_handle* h);
+
+/* Solve B instances (Sec. 2.3 SCP loop; all of Sec. 2.3.1-3 per iteration).
+ *   x0        device [B][14]
+ *   n_nodes   device [B] (2..n_max) or NULL for n_max everywhere
+ *   mode      0: plain form, one launch per phase per SCP iteration, the
+ *                iteration captured once in a CUDA graph and replayed;
+ *             1: persistent form, one launch, each CTA takes instances from
+ *                a work queue until none is left.
+ *   X, U      device outputs (see layouts)
+ *   tf, fuel  device [B]: final time sum_k dtau (s_k + s_{k+1})/2 and m_1 - m_N
+ *   status    device [B] PDG_CONVERGED ... PDG_BAD_INPUT
+ *   scp_iters device [B]; pipg_iters device [B] (sum over SCP iterations)
+ *   trace     device [B][scp_jmax][2] (power iterations, PIPG iterations per
+ *             SCP iteration; zero past the last) or NULL
+ * The plain form synchronizes the stream once per SCP iteration to stop early
+ * when every instance is done. */
+int pdg_mc_solve_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes, int mode,
+                       double* X, double* U, double* tf, double* fuel, int* status,
+                       int* scp_iters, long long* pipg_iters, int* trace, void* cuda_stream);
+
+/* Same as pdg_mc_solve_batch with HOST buffers (pageable or pinned): copies
+ * x0 / n_nodes in and the outputs back through handle-owned device buffers on
+ * the stream, and returns after the stream has drained. */
+int pdg_mc_solve_batch_host(pdg_handle* h, int B, const double* x0, const int* n_nodes, int mode,
+                            double* X, double* U, double* tf, double* fuel, int* status,
+                            int* scp_iters, long long* pipg_iters, void* cuda_stream);
+
+/* Scaled subproblem data about a reference (X, U) (Sec. 2.3.1 STM IVP by RK4
+ * with rk4_substeps substeps per interval, then the prescaling of Sec. 2.3.2):
+ *   Am  device [B][n_max-1][15][15]   hat A^-_k = P_x^-1 A_k P_x
+ *   Bm  device [B][n_max-1][15][nu]   hat B^-_k = P_x^-1 B^-_k P_u
+ *   Bp  device [B][n_max-1][15][nu]   hat B^+_k
+ *   w   device [B][n_max-1][15]       hat w_k = P_x^-1 (xbar^k(tau_{k+1}) - xbar_{k+1})
+ * Inputs x0, n_nodes, X, U as above (device).  Rows past n_nodes-1 are zero. */
+int pdg_mc_subproblem(pdg_handle* h, int B, const double* x0, const int* n_nodes,
+                      const double* X, const double* U,
+                      double* Am, double* Bm, double* Bp, double* w, void* cuda_stream);
+
+/* One SCP iteration in place (plain-form kernels): discretize and scale about
+ * (X, U), power iteration, PIPG_custom warm-started from (xh, uh, mup, mum,
+ * phi, th), then X += P_x xh, U += P_u uh.  Device buffers:
+ *   X [B][n_max][15], U [B][n_max][nu]         reference in / updated out
+ *   xh [B][n_max][15], uh [B][n_max][nu], mup, mum, phi [B][n_max-1][15],
+ *   th [B][n_max-1]                             warm start in / solution out
+ *   force [B][2] (power, PIPG) iteration counts to run exactly, or NULL
+ *   sigma [B], defect [B] (max |hat w|), step [B] (max |xh|, |uh|) outputs
+ *   iters [B][2] (power, PIPG) outputs. */
+int pdg_mc_scp_step(pdg_handle* h, int B, const double* x0, const int* n_nodes,
+                    double* X, double* U, double* xh, double* uh, double* mup, double* mum,
+                    double* phi, double* th, const int* force,
+                    double* sigma, double* defect, double* step, int* iters, void* cuda_stream);
+
+/* Shape of the last launch configuration chosen for (n_max, nu, precision):
+ * threads per CTA, CTAs per SM and dynamic shared memory per CTA (bytes).
+ * Synchronous; no device work. */
+int pdg_mc_launch_info(pdg_handle* h, int* threads, int* ctas_per_sm, int* smem_bytes);
+
+/* Override the threads-per-CTA of the solve kernels (multiple of 32, 0 =
+ * automatic).  Used by the autotuner. */
+int pdg_mc_set_threads(pdg_handle* h, int threads);
+
+/* Roofline denominator probe (no counterpart in the paper): runs an FMA-chain
+ * kernel on all SMs of the current device in FP64 (precision 0) or FP32 (1)
+ * and writes the best of three timed launches, in TFLOP/s, to *tflops.
+ * Synchronizes the stream; allocates 16 bytes of device memory. */
+int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

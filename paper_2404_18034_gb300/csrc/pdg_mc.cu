@@ -1,0 +1,865 @@
+// pdg_mc.cu -- kernels and C ABI of the batched GB300 solver for Monte Carlo
+// 6-DoF powered-descent guidance (arXiv 2404.18034).  See include/pdg_mc.h.
+//
+// Two execution forms share the device phases of pdg_phases.cuh:
+//  * persistent: one launch; each CTA takes instance ids from a global work
+//    queue (atomicAdd), runs the whole SCP solve with every block of the
+//    instance in shared memory, writes the result and takes the next id, so
+//    instances of uneven size and iteration count retire and refill freely;
+//  * plain: one launch per phase (discretize+scale, power iteration, PIPG,
+//    update) per SCP iteration, the per-instance image kept in global memory
+//    between launches; the four launches of an SCP iteration are captured
+//    once in a CUDA graph and replayed until every instance is done.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/pdg_mc.h"
+#include "pdg_phases.cuh"
+
+using namespace pdg;
+
+namespace {
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename R>
+__device__ __forceinline__ void copy_g2s(R* dst, const R* src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+template <typename R>
+__device__ __forceinline__ void copy_s2g(R* dst, const R* src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// Load x0 of instance b into the image (x0[14], y = 0); returns false when it
+// is not finite.  Every thread returns the same value.
+template <typename R>
+__device__ bool load_x0(const Lay& L, R* sm, const double* __restrict__ x0, int b) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    double v = threadIdx.x < 14 ? x0[(size_t)b * 14 + threadIdx.x] : 0.0;
+    if (!isfinite(v)) atomicOr(&bad, 1);
+    sm[L.x0 + threadIdx.x] = R(v);
+  }
+  __syncthreads();
+  const bool ok = bad == 0;
+  __syncthreads();
+  return ok;
+}
+
+template <typename R, int NU>
+__device__ void write_outputs(const Lay& L, const R* sm, int b, int Nmax, int status, int scp, long long pipg,
+                              double* X, double* U, double* tf, double* fuel, int* st, int* sit, long long* pit) {
+  const int N = L.N;
+  double* Xo = X + (size_t)b * Nmax * NX;
+  double* Uo = U + (size_t)b * Nmax * NU;
+  const bool ok = status != PDG_BAD_INPUT;
+  for (int t = threadIdx.x; t < Nmax * NX; t += blockDim.x) Xo[t] = (ok && t < N * NX) ? double(sm[L.Xb + t]) : 0.0;
+  for (int t = threadIdx.x; t < Nmax * NU; t += blockDim.x) Uo[t] = (ok && t < N * NU) ? double(sm[L.Ub + t]) : 0.0;
+  if (threadIdx.x == 0) {
+    double t_f = 0.0, fu = 0.0;
+    if (ok) {
+      for (int k = 0; k < N - 1; ++k)
+        t_f += 0.5 * (double(sm[L.Ub + k * NU + NU - 1]) + double(sm[L.Ub + (k + 1) * NU + NU - 1])) / double(N - 1);
+      fu = double(sm[L.Xb + IM]) - double(sm[L.Xb + (N - 1) * NX + IM]);
+    }
+    tf[b] = t_f;
+    fuel[b] = fu;
+    st[b] = status;
+    sit[b] = scp;
+    pit[b] = pipg;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// persistent form
+// ---------------------------------------------------------------------------
+template <typename R, int NU>
+__global__ void __launch_bounds__(512, 1)
+k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
+             double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
+             int* trace, int* queue) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  __shared__ int inst;
+  for (;;) {
+    if (threadIdx.x == 0) inst = atomicAdd(queue, 1);
+    __syncthreads();
+    const int b = inst;
+    __syncthreads();
+    if (b >= B) break;
+    const int N = Ns ? Ns[b] : Nmax;
+    if (N < 2 || N > Nmax) {
+      Lay L0 = make_lay(2, NU, blockDim.x);
+      write_outputs<R, NU>(L0, sm, b, Nmax, PDG_BAD_INPUT, 0, 0, X, U, tf, fuel, status, scp_iters, pipg_iters);
+      __syncthreads();
+      continue;
+    }
+    const Lay L = make_lay(N, NU, blockDim.x);
+    if (!load_x0<R>(L, sm, x0, b)) {
+      write_outputs<R, NU>(L, sm, b, Nmax, PDG_BAD_INPUT, 0, 0, X, U, tf, fuel, status, scp_iters, pipg_iters);
+      __syncthreads();
+      continue;
+    }
+    const unsigned long long t_start = globaltimer_ns();
+    phase_init_guess<R, NU>(P, L, sm);
+    for (int t = threadIdx.x; t < L.img - L.xh; t += blockDim.x) sm[L.xh + t] = R(0);
+    __syncthreads();
+    int stat = PDG_MAX_SCP, j;
+    long long ptot = 0;
+    for (j = 1; j <= P.scp_jmax; ++j) {
+      if (P.budget_ns > 0.0 && double(globaltimer_ns() - t_start) > P.budget_ns) { stat = PDG_BUDGET; --j; break; }
+      const R defect = phase_discretize<R, NU>(P, L, sm);
+      phase_scale_extra<R, NU>(P, L, sm);
+      __syncthreads();
+      int pit;
+      const R sigma = phase_power<R, NU>(P, L, sm, 0, &pit);
+      const int jit = phase_pipg<R, NU>(P, L, sm, sigma, 0);
+      bool bad;
+      const R step = phase_update<R, NU>(P, L, sm, &bad);
+      ptot += jit;
+      if (trace && threadIdx.x == 0) {
+        trace[((size_t)b * P.scp_jmax + (j - 1)) * 2 + 0] = pit;
+        trace[((size_t)b * P.scp_jmax + (j - 1)) * 2 + 1] = jit;
+      }
+      if (bad) { stat = PDG_NONFINITE; break; }
+      const R dy = sm[L.Xb + (N - 1) * NX + IY] - sm[L.Xb + IY];
+      if (step <= R(P.scp_eps_step) && defect <= R(P.scp_eps_defect) && dy <= R(N - 1) * R(P.eps_ctcs)) {
+        stat = PDG_CONVERGED;
+        break;
+      }
+    }
+    if (j > P.scp_jmax) j = P.scp_jmax;
+    if (trace) {
+      for (int t = threadIdx.x + 2 * j; t < 2 * P.scp_jmax; t += blockDim.x) trace[(size_t)b * P.scp_jmax * 2 + t] = 0;
+    }
+    write_outputs<R, NU>(L, sm, b, Nmax, stat, j, ptot, X, U, tf, fuel, status, scp_iters, pipg_iters);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// plain form: per-instance image in global memory between launches
+// ---------------------------------------------------------------------------
+struct PlainWs {
+  void* img;           // [B][istride] of R
+  int istride;         // elements of R per instance
+  int* st;             // [B] running / final status
+  int* sit;            // [B] SCP iterations done
+  long long* lit;      // [B] PIPG iterations summed
+  int* pow_it;         // [B] last power iterations
+  int* pipg_it;        // [B] last PIPG iterations
+  int* done;           // [1] instances finished
+};
+
+template <typename R, int NU>
+__global__ void __launch_bounds__(512, 1)
+k_plain_init(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns, PlainWs W,
+             double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  const int b = blockIdx.x;
+  const int N = Ns ? Ns[b] : Nmax;
+  R* img = reinterpret_cast<R*>(W.img) + (size_t)b * W.istride;
+  if (threadIdx.x == 0) { W.sit[b] = 0; W.lit[b] = 0; }
+  if (N < 2 || N > Nmax) {
+    Lay L0 = make_lay(2, NU, blockDim.x);
+    if (threadIdx.x == 0) { W.st[b] = PDG_BAD_INPUT; atomicAdd(W.done, 1); }
+    write_outputs<R, NU>(L0, sm, b, Nmax, PDG_BAD_INPUT, 0, 0, X, U, tf, fuel, status, scp_iters, pipg_iters);
+    return;
+  }
+  const Lay L = make_lay(N, NU, blockDim.x);
+  if (!load_x0<R>(L, sm, x0, b)) {
+    if (threadIdx.x == 0) { W.st[b] = PDG_BAD_INPUT; atomicAdd(W.done, 1); }
+    write_outputs<R, NU>(L, sm, b, Nmax, PDG_BAD_INPUT, 0, 0, X, U, tf, fuel, status, scp_iters, pipg_iters);
+    return;
+  }
+  phase_init_guess<R, NU>(P, L, sm);
+  for (int t = threadIdx.x; t < L.img - L.xh; t += blockDim.x) sm[L.xh + t] = R(0);
+  __syncthreads();
+  copy_s2g(img, sm, L.img);
+  if (threadIdx.x == 0) W.st[b] = ST_RUNNING;
+}
+
+template <typename R, int NU>
+__global__ void __launch_bounds__(512, 1)
+k_plain_disc(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  const int b = blockIdx.x;
+  if (W.st[b] != ST_RUNNING) return;
+  const int N = Ns ? Ns[b] : Nmax;
+  const Lay L = make_lay(N, NU, blockDim.x);
+  R* img = reinterpret_cast<R*>(W.img) + (size_t)b * W.istride;
+  copy_g2s(sm + L.x0, img + L.x0, L.Am - L.x0);  // x0, Xb, Ub
+  __syncthreads();
+  const R defect = phase_discretize<R, NU>(P, L, sm);
+  phase_scale_extra<R, NU>(P, L, sm);
+  __syncthreads();
+  copy_s2g(img + L.Am, sm + L.Am, L.xh - L.Am);  // Am .. zf
+  if (threadIdx.x == 0) img[L.sc + 1] = defect;
+}
+
+template <typename R, int NU>
+__global__ void __launch_bounds__(512, 1)
+k_plain_power(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, const int* force) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  const int b = blockIdx.x;
+  if (W.st[b] != ST_RUNNING) return;
+  const int N = Ns ? Ns[b] : Nmax;
+  const Lay L = make_lay(N, NU, blockDim.x);
+  R* img = reinterpret_cast<R*>(W.img) + (size_t)b * W.istride;
+  copy_g2s(sm + L.Am, img + L.Am, L.w - L.Am);        // Am, Bm, Bp
+  copy_g2s(sm + L.xh, img + L.xh, L.phi - L.xh);      // xh, uh, mup, mum
+  __syncthreads();
+  int it;
+  const R sigma = phase_power<R, NU>(P, L, sm, force ? force[2 * b] : 0, &it);
+  if (threadIdx.x == 0) { img[L.sc + 0] = sigma; W.pow_it[b] = it; }
+}
+
+template <typename R, int NU>
+__global__ void __launch_bounds__(512, 1)
+k_plain_pipg(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, const int* force) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  const int b = blockIdx.x;
+  if (W.st[b] != ST_RUNNING) return;
+  const int N = Ns ? Ns[b] : Nmax;
+  const Lay L = make_lay(N, NU, blockDim.x);
+  R* img = reinterpret_cast<R*>(W.img) + (size_t)b * W.istride;
+  copy_g2s(sm + L.Am, img + L.Am, L.img - L.Am);     // subproblem + warm start
+  __syncthreads();
+  const R sigma = img[L.sc + 0];
+  const int it = phase_pipg<R, NU>(P, L, sm, sigma, force ? force[2 * b + 1] : 0);
+  copy_s2g(img + L.xh, sm + L.xh, L.img - L.xh);
+  if (threadIdx.x == 0) W.pipg_it[b] = it;
+}
+
+// step_only: the one-iteration API (no status, no outputs).
+template <typename R, int NU>
+__global__ void __launch_bounds__(512, 1)
+k_plain_update(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, int step_only,
+               double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
+               int* trace, double* step_out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  const int b = blockIdx.x;
+  if (W.st[b] != ST_RUNNING) return;
+  const int N = Ns ? Ns[b] : Nmax;
+  const Lay L = make_lay(N, NU, blockDim.x);
+  R* img = reinterpret_cast<R*>(W.img) + (size_t)b * W.istride;
+  copy_g2s(sm + L.Xb, img + L.Xb, L.Am - L.Xb);      // Xb, Ub
+  copy_g2s(sm + L.xh, img + L.xh, L.mup - L.xh);     // xh, uh
+  __syncthreads();
+  bool bad;
+  const R step = phase_update<R, NU>(P, L, sm, &bad);
+  copy_s2g(img + L.Xb, sm + L.Xb, L.Am - L.Xb);
+  if (step_only) {
+    if (threadIdx.x == 0) step_out[b] = double(step);
+    return;
+  }
+  const int j = W.sit[b] + 1;
+  const long long ptot = W.lit[b] + W.pipg_it[b];
+  if (trace && threadIdx.x == 0) {
+    trace[((size_t)b * P.scp_jmax + (j - 1)) * 2 + 0] = W.pow_it[b];
+    trace[((size_t)b * P.scp_jmax + (j - 1)) * 2 + 1] = W.pipg_it[b];
+  }
+  const R defect = img[L.sc + 1];
+  const R dy = sm[L.Xb + (N - 1) * NX + IY] - sm[L.Xb + IY];
+  int stat = ST_RUNNING;
+  if (bad) stat = PDG_NONFINITE;
+  else if (step <= R(P.scp_eps_step) && defect <= R(P.scp_eps_defect) && dy <= R(N - 1) * R(P.eps_ctcs)) stat = PDG_CONVERGED;
+  else if (j >= P.scp_jmax) stat = PDG_MAX_SCP;
+  __syncthreads();
+  if (threadIdx.x == 0) { W.sit[b] = j; W.lit[b] = ptot; }
+  if (stat != ST_RUNNING) {
+    if (trace) {
+      for (int t = threadIdx.x + 2 * j; t < 2 * P.scp_jmax; t += blockDim.x) trace[(size_t)b * P.scp_jmax * 2 + t] = 0;
+    }
+    write_outputs<R, NU>(L, sm, b, Nmax, stat, j, ptot, X, U, tf, fuel, status, scp_iters, pipg_iters);
+    if (threadIdx.x == 0) { W.st[b] = stat; atomicAdd(W.done, 1); }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// API helpers: subproblem data and one-iteration packing
+// ---------------------------------------------------------------------------
+template <typename R, int NU>
+__global__ void __launch_bounds__(512, 1)
+k_subproblem(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
+             const double* __restrict__ X, const double* __restrict__ U, double* Am, double* Bm, double* Bp, double* w) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  const int b = blockIdx.x;
+  const int N = Ns ? Ns[b] : Nmax;
+  const size_t oA = (size_t)b * (Nmax - 1) * NX * NX, oB = (size_t)b * (Nmax - 1) * NX * NU, ow = (size_t)b * (Nmax - 1) * NX;
+  if (N < 2 || N > Nmax) return;
+  const Lay L = make_lay(N, NU, blockDim.x);
+  load_x0<R>(L, sm, x0, b);
+  for (int t = threadIdx.x; t < N * NX; t += blockDim.x) sm[L.Xb + t] = R(X[(size_t)b * Nmax * NX + t]);
+  for (int t = threadIdx.x; t < N * NU; t += blockDim.x) sm[L.Ub + t] = R(U[(size_t)b * Nmax * NU + t]);
+  __syncthreads();
+  phase_discretize<R, NU>(P, L, sm);
+  __syncthreads();
+  for (int t = threadIdx.x; t < (Nmax - 1) * NX * NX; t += blockDim.x) Am[oA + t] = t < (N - 1) * NX * NX ? double(sm[L.Am + t]) : 0.0;
+  for (int t = threadIdx.x; t < (Nmax - 1) * NX * NU; t += blockDim.x) {
+    Bm[oB + t] = t < (N - 1) * NX * NU ? double(sm[L.Bm + t]) : 0.0;
+    Bp[oB + t] = t < (N - 1) * NX * NU ? double(sm[L.Bp + t]) : 0.0;
+  }
+  for (int t = threadIdx.x; t < (Nmax - 1) * NX; t += blockDim.x) w[ow + t] = t < (N - 1) * NX ? double(sm[L.w + t]) : 0.0;
+}
+
+// dir = 0: user buffers -> image (and mark running); dir = 1: image -> user.
+template <typename R, int NU>
+__global__ void k_pack(int B, int Nmax, int threads, const double* __restrict__ x0, const int* __restrict__ Ns, PlainWs W,
+                       int dir, double* X, double* U, double* xh, double* uh, double* mup, double* mum, double* phi,
+                       double* th, double* sigma, double* defect, int* iters) {
+  const int b = blockIdx.x;
+  const int N = Ns ? Ns[b] : Nmax;
+  if (N < 2 || N > Nmax) {
+    if (dir == 0 && threadIdx.x == 0) W.st[b] = PDG_BAD_INPUT;
+    return;
+  }
+  const Lay L = make_lay(N, NU, threads);
+  R* img = reinterpret_cast<R*>(W.img) + (size_t)b * W.istride;
+  struct Seg { int off, n; double* p; size_t stride; };
+  const Seg segs[8] = {
+      {L.Xb, N * NX, X, (size_t)Nmax * NX},          {L.Ub, N * NU, U, (size_t)Nmax * NU},
+      {L.xh, N * NX, xh, (size_t)Nmax * NX},         {L.uh, N * NU, uh, (size_t)Nmax * NU},
+      {L.mup, (N - 1) * NX, mup, (size_t)(Nmax - 1) * NX}, {L.mum, (N - 1) * NX, mum, (size_t)(Nmax - 1) * NX},
+      {L.phi, (N - 1) * NX, phi, (size_t)(Nmax - 1) * NX}, {L.th, N - 1, th, (size_t)(Nmax - 1)}};
+  for (int s = 0; s < 8; ++s) {
+    double* p = segs[s].p + (size_t)b * segs[s].stride;
+    for (int t = threadIdx.x; t < segs[s].n; t += blockDim.x) {
+      if (dir == 0) img[segs[s].off + t] = R(p[t]);
+      else p[t] = double(img[segs[s].off + t]);
+    }
+  }
+  if (dir == 0) {
+    for (int t = threadIdx.x; t < 16; t += blockDim.x) img[L.x0 + t] = t < 14 ? R(x0[(size_t)b * 14 + t]) : R(0);
+    if (threadIdx.x == 0) W.st[b] = ST_RUNNING;
+  } else if (threadIdx.x == 0) {
+    sigma[b] = double(img[L.sc + 0]);
+    defect[b] = double(img[L.sc + 1]);
+    iters[2 * b] = W.pow_it[b];
+    iters[2 * b + 1] = W.pipg_it[b];
+  }
+}
+
+// FMA-chain probe for the roofline denominator: every thread runs 8
+// independent dependency chains of `iters` FMAs each (16 flops per step).
+template <typename R>
+__global__ void k_fma_probe(int iters, R seed, R* out) {
+  R a0 = seed + R(threadIdx.x), a1 = a0 + R(1), a2 = a0 + R(2), a3 = a0 + R(3);
+  R a4 = a0 + R(4), a5 = a0 + R(5), a6 = a0 + R(6), a7 = a0 + R(7);
+  const R m = R(0.999999), c = R(1e-7);
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+    a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+  }
+  const R s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == R(-12345)) out[0] = s;  // keeps the chains live; never true
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side
+// ===========================================================================
+struct pdg_handle {
+  pdg_params p;
+  DParams dp;
+  int n_max;
+  int threads_override;
+  int device;
+  int num_sms;
+  std::string err;
+  // plain-form workspace
+  void* img = nullptr;
+  size_t img_bytes = 0;
+  int* ints = nullptr;        // st, sit, pow_it, pipg_it, done, queue
+  size_t ints_count = 0;
+  long long* lit = nullptr;
+  size_t lit_count = 0;
+  int* pinned_done = nullptr;
+  cudaStream_t cap = nullptr;  // plain form runs (and is captured) here
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // host-buffer API staging
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  // last launch
+  int last_threads = 0, last_ctas = 0, last_smem = 0;
+};
+
+static std::string g_init_err;
+
+#define PDG_CUDA(h, call)                                                        \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);            \
+      return PDG_ECUDA;                                                          \
+    }                                                                            \
+  } while (0)
+
+static int fail(pdg_handle* h, int code, const std::string& msg) {
+  h->err = msg;
+  return code;
+}
+
+static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
+  memset(d, 0, sizeof *d);
+  if (!(p->nu == 4 || p->nu == 7)) { *why = "nu must be 4 or 7"; return false; }
+  if (!(p->precision == 0 || p->precision == 1)) { *why = "precision must be 0 (FP64) or 1 (FP32)"; return false; }
+  if (p->rk4_substeps < 1 || p->pipg_jmax < 1 || p->pipg_jcheck < 1 || p->pow_jmax < 1 || p->scp_jmax < 1) {
+    *why = "iteration counts and rk4_substeps must be >= 1"; return false;
+  }
+  for (int i = 0; i < 3; ++i) if (!(p->J_B[i] > 0)) { *why = "J_B must be positive"; return false; }
+  for (int i = 0; i < 15; ++i) if (!(p->P_x[i] > 0)) { *why = "P_x must be positive"; return false; }
+  for (int i = 0; i < 3; ++i) if (!(p->P_u[i] > 0)) { *why = "P_u must be positive"; return false; }
+  if (p->nu == 7) for (int i = 3; i < 6; ++i) if (!(p->P_u[i] > 0)) { *why = "P_u must be positive"; return false; }
+  if (!(p->P_u[p->nu - 1] > 0)) { *why = "P_u must be positive"; return false; }
+  if (!(p->w_prox > 0) || !(p->pipg_omega > 0) || !(p->s_max >= p->s_min)) { *why = "w_prox, pipg_omega > 0 and s_min <= s_max required"; return false; }
+  d->nu = p->nu;
+  d->nsub = p->rk4_substeps;
+  d->pipg_jmax = p->pipg_jmax;
+  d->pipg_jcheck = p->pipg_jcheck;
+  d->pow_jmax = p->pow_jmax;
+  d->scp_jmax = p->scp_jmax;
+  for (int i = 0; i < 15; ++i) d->fix_f[i] = p->fix_f[i] ? 1 : 0;
+  d->alpha_mdot = p->alpha_mdot;
+  for (int i = 0; i < 3; ++i) {
+    d->g[i] = p->g_I[i];
+    d->J[i] = p->J_B[i];
+    d->Jinv[i] = 1.0 / p->J_B[i];
+    d->rT[i] = p->r_T_B[i];
+  }
+  d->m_dry = p->m_dry;
+  d->vmax2 = p->v_max * p->v_max;
+  d->one_m_cos_theta = 1.0 - cos(p->theta_max);
+  d->omega_max2 = p->omega_max * p->omega_max;
+  d->sec_delta = 1.0 / cos(p->delta_max);
+  d->T_min = p->T_min;
+  d->T_max = p->T_max;
+  d->gamma_max2 = p->gamma_max * p->gamma_max;
+  d->s_min = p->s_min;
+  d->s_max = p->s_max;
+  for (int i = 0; i < 15; ++i) {
+    d->z_f[i] = p->z_f[i];
+    d->Px[i] = p->P_x[i];
+    d->Pxinv[i] = 1.0 / p->P_x[i];
+  }
+  for (int i = 0; i < 7; ++i) {
+    d->Pu[i] = p->P_u[i];
+    d->Puinv[i] = p->P_u[i] > 0 ? 1.0 / p->P_u[i] : 0.0;
+  }
+  d->w_cost = p->w_cost;
+  d->w_prox = p->w_prox;
+  d->w_ep = p->w_ep;
+  d->eps_ctcs = p->eps_ctcs;
+  d->omega = p->pipg_omega;
+  d->rho = p->pipg_rho;
+  d->eps_abs = p->pipg_eps_abs;
+  d->eps_rel = p->pipg_eps_rel;
+  d->pow_eps_abs = p->pow_eps_abs;
+  d->pow_eps_rel = p->pow_eps_rel;
+  d->pow_buff = p->pow_eps_buff;
+  d->scp_eps_step = p->scp_eps_step;
+  d->scp_eps_defect = p->scp_eps_defect;
+  d->tf_guess = p->tf_guess;
+  d->g0 = sqrt(p->g_I[0] * p->g_I[0] + p->g_I[1] * p->g_I[1] + p->g_I[2] * p->g_I[2]);
+  d->budget_ns = p->budget_seconds > 0 ? p->budget_seconds * 1e9 : 0.0;
+  return true;
+}
+
+
+// Threads per CTA: enough for one discretization wave of the largest instance
+// (capped at 512) and at least two PIPG dual rows per thread.
+static int pick_threads(const pdg_handle* h) {
+  if (h->threads_override > 0) return h->threads_override;
+  const int nu = h->p.nu, N = h->n_max;
+  const int per = 15 + 2 * nu + 1;
+  int t = (N - 1) * per;
+  const int dual = (N - 1) * 16;
+  if (t < dual) t = dual;
+  t = (t + 31) / 32 * 32;
+  if (t > 512) t = 512;
+  if (t < 128) t = 128;
+  return t;
+}
+
+template <typename R, int NU>
+struct Kern {
+  static int prepare(pdg_handle* h, int threads, size_t smem) {
+    const void* fns[] = {(const void*)k_persistent<R, NU>, (const void*)k_plain_init<R, NU>, (const void*)k_plain_disc<R, NU>,
+                         (const void*)k_plain_power<R, NU>, (const void*)k_plain_pipg<R, NU>, (const void*)k_plain_update<R, NU>,
+                         (const void*)k_subproblem<R, NU>};
+    for (const void* f : fns) PDG_CUDA(h, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return 0;
+  }
+};
+
+template <typename R, int NU>
+static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int mode, double* X, double* U, double* tf,
+                     double* fuel, int* status, int* scp_iters, long long* pipg_iters, int* trace, cudaStream_t s) {
+  const int T = pick_threads(h);
+  const Lay L = make_lay(h->n_max, NU, T);
+  const size_t smem = (size_t)L.total * sizeof(R);
+  if (L.ipw < 1) return fail(h, PDG_EINVAL, "threads per CTA too small for one discretization interval");
+  if (int rc = Kern<R, NU>::prepare(h, T, smem)) return rc;
+  int occ = 0;
+  PDG_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persistent<R, NU>, T, smem));
+  if (occ < 1) return fail(h, PDG_EINVAL, "solve kernel does not fit on an SM with this configuration");
+  h->last_threads = T;
+  h->last_ctas = occ;
+  h->last_smem = (int)smem;
+  // integer workspace: st, sit, pow_it, pipg_it [B each], done, queue
+  const size_t nints = (size_t)4 * B + 2;
+  if (h->ints_count < nints) {
+    if (h->ints) cudaFree(h->ints);
+    h->ints = nullptr;
+    h->ints_count = 0;
+    PDG_CUDA(h, cudaMalloc(&h->ints, nints * sizeof(int)));
+    h->ints_count = nints;
+  }
+  int* queue = h->ints + 4 * (size_t)B + 1;
+  if (mode == 1) {
+    PDG_CUDA(h, cudaMemsetAsync(queue, 0, sizeof(int), s));
+    const int grid = (int)((long long)occ * h->num_sms < B ? (long long)occ * h->num_sms : B);
+    k_persistent<R, NU><<<grid, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, X, U, tf, fuel, status, scp_iters, pipg_iters,
+                                              trace, queue);
+    PDG_CUDA(h, cudaGetLastError());
+    return 0;
+  }
+  // plain form
+  const Lay Li = make_lay(h->n_max, NU, T);
+  const size_t istride = (size_t)Li.img;
+  const size_t need = istride * sizeof(R) * B;
+  if (h->img_bytes < need) {
+    if (h->img) cudaFree(h->img);
+    h->img = nullptr;
+    h->img_bytes = 0;
+    PDG_CUDA(h, cudaMalloc(&h->img, need));
+    h->img_bytes = need;
+  }
+  if (h->lit_count < (size_t)B) {
+    if (h->lit) cudaFree(h->lit);
+    h->lit = nullptr;
+    h->lit_count = 0;
+    PDG_CUDA(h, cudaMalloc(&h->lit, sizeof(long long) * B));
+    h->lit_count = B;
+  }
+  if (!h->pinned_done) PDG_CUDA(h, cudaMallocHost(&h->pinned_done, sizeof(int)));
+  if (!h->cap) PDG_CUDA(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  if (!h->ev_in) PDG_CUDA(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  if (!h->ev_out) PDG_CUDA(h, cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  // the caller's stream may be the legacy default stream, which cannot be
+  // captured: run on the handle's stream, ordered after and before the caller's
+  const cudaStream_t us = s;
+  PDG_CUDA(h, cudaEventRecord(h->ev_in, us));
+  PDG_CUDA(h, cudaStreamWaitEvent(h->cap, h->ev_in, 0));
+  s = h->cap;
+  PlainWs W;
+  W.img = h->img;
+  W.istride = (int)istride;
+  W.st = h->ints;
+  W.sit = h->ints + B;
+  W.pow_it = h->ints + 2 * (size_t)B;
+  W.pipg_it = h->ints + 3 * (size_t)B;
+  W.done = h->ints + 4 * (size_t)B;
+  W.lit = h->lit;
+  PDG_CUDA(h, cudaMemsetAsync(W.done, 0, sizeof(int), s));
+  k_plain_init<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, W, X, U, tf, fuel, status, scp_iters, pipg_iters);
+  PDG_CUDA(h, cudaGetLastError());
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  PDG_CUDA(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  k_plain_disc<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W);
+  k_plain_power<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
+  k_plain_pipg<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
+  k_plain_update<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, 0, X, U, tf, fuel, status, scp_iters, pipg_iters,
+                                            trace, nullptr);
+  cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  if (ce != cudaSuccess) return fail(h, PDG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(h, PDG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+  }
+  int rc = 0;
+  for (int j = 0; j < h->p.scp_jmax; ++j) {
+    ce = cudaGraphLaunch(exec, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h->pinned_done, W.done, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) { rc = fail(h, PDG_ECUDA, std::string("plain SCP step: ") + cudaGetErrorString(ce)); break; }
+    if (*h->pinned_done >= B) break;
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (rc == 0) {
+    PDG_CUDA(h, cudaEventRecord(h->ev_out, s));
+    PDG_CUDA(h, cudaStreamWaitEvent(us, h->ev_out, 0));
+  }
+  return rc;
+}
+
+template <typename R, int NU>
+static int run_subproblem(pdg_handle* h, int B, const double* x0, const int* Ns, const double* X, const double* U,
+                          double* Am, double* Bm, double* Bp, double* w, cudaStream_t s) {
+  const int T = pick_threads(h);
+  const Lay L = make_lay(h->n_max, NU, T);
+  const size_t smem = (size_t)L.total * sizeof(R);
+  if (int rc = Kern<R, NU>::prepare(h, T, smem)) return rc;
+  k_subproblem<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, X, U, Am, Bm, Bp, w);
+  PDG_CUDA(h, cudaGetLastError());
+  return 0;
+}
+
+template <typename R, int NU>
+static int run_step(pdg_handle* h, int B, const double* x0, const int* Ns, double* X, double* U, double* xh, double* uh,
+                    double* mup, double* mum, double* phi, double* th, const int* force, double* sigma, double* defect,
+                    double* step, int* iters, cudaStream_t s) {
+  const int T = pick_threads(h);
+  const Lay L = make_lay(h->n_max, NU, T);
+  const size_t smem = (size_t)L.total * sizeof(R);
+  if (int rc = Kern<R, NU>::prepare(h, T, smem)) return rc;
+  const size_t istride = (size_t)L.img;
+  const size_t need = istride * sizeof(R) * B;
+  if (h->img_bytes < need) {
+    if (h->img) cudaFree(h->img);
+    h->img = nullptr;
+    h->img_bytes = 0;
+    PDG_CUDA(h, cudaMalloc(&h->img, need));
+    h->img_bytes = need;
+  }
+  const size_t nints = (size_t)4 * B + 2;
+  if (h->ints_count < nints) {
+    if (h->ints) cudaFree(h->ints);
+    h->ints = nullptr;
+    h->ints_count = 0;
+    PDG_CUDA(h, cudaMalloc(&h->ints, nints * sizeof(int)));
+    h->ints_count = nints;
+  }
+  if (h->lit_count < (size_t)B) {
+    if (h->lit) cudaFree(h->lit);
+    h->lit = nullptr;
+    h->lit_count = 0;
+    PDG_CUDA(h, cudaMalloc(&h->lit, sizeof(long long) * B));
+    h->lit_count = B;
+  }
+  PlainWs W;
+  W.img = h->img;
+  W.istride = (int)istride;
+  W.st = h->ints;
+  W.sit = h->ints + B;
+  W.pow_it = h->ints + 2 * (size_t)B;
+  W.pipg_it = h->ints + 3 * (size_t)B;
+  W.done = h->ints + 4 * (size_t)B;
+  W.lit = h->lit;
+  k_pack<R, NU><<<B, 128, 0, s>>>(B, h->n_max, T, x0, Ns, W, 0, X, U, xh, uh, mup, mum, phi, th, sigma, defect, iters);
+  k_plain_disc<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W);
+  k_plain_power<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, force);
+  k_plain_pipg<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, force);
+  k_plain_update<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, 1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                            nullptr, nullptr, nullptr, step);
+  k_pack<R, NU><<<B, 128, 0, s>>>(B, h->n_max, T, x0, Ns, W, 1, X, U, xh, uh, mup, mum, phi, th, sigma, defect, iters);
+  PDG_CUDA(h, cudaGetLastError());
+  return 0;
+}
+
+#define PDG_DISPATCH(h, fn, ...)                                         \
+  ((h)->p.precision == 0                                                 \
+       ? ((h)->p.nu == 4 ? fn<double, 4>(__VA_ARGS__) : fn<double, 7>(__VA_ARGS__)) \
+       : ((h)->p.nu == 4 ? fn<float, 4>(__VA_ARGS__) : fn<float, 7>(__VA_ARGS__)))
+
+extern "C" {
+
+int pdg_mc_init(const pdg_params* p, int n_max, pdg_handle** out) {
+  if (!out) { g_init_err = "out is NULL"; return PDG_EINVAL; }
+  *out = nullptr;
+  if (!p) { g_init_err = "params is NULL"; return PDG_EINVAL; }
+  if (n_max < 2 || n_max > NMAX) { g_init_err = "n_max must be in [2, 32]"; return PDG_EINVAL; }
+  DParams d;
+  std::string why;
+  if (!fill_dparams(p, &d, &why)) { g_init_err = why; return PDG_EINVAL; }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) { g_init_err = std::string("no usable CUDA device: ") + cudaGetErrorString(e); return PDG_ECUDA; }
+  pdg_handle* h = new (std::nothrow) pdg_handle();
+  if (!h) { g_init_err = "out of host memory"; return PDG_ENOMEM; }
+  h->p = *p;
+  h->dp = d;
+  h->n_max = n_max;
+  h->threads_override = 0;
+  h->device = dev;
+  h->num_sms = sms;
+  *out = h;
+  g_init_err.clear();
+  return PDG_OK;
+}
+
+void pdg_mc_destroy(pdg_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  if (h->img) cudaFree(h->img);
+  if (h->ints) cudaFree(h->ints);
+  if (h->lit) cudaFree(h->lit);
+  if (h->stage) cudaFree(h->stage);
+  if (h->pinned_done) cudaFreeHost(h->pinned_done);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  delete h;
+}
+
+const char* pdg_mc_last_error(const pdg_handle* h) { return h ? h->err.c_str() : g_init_err.c_str(); }
+
+int pdg_mc_solve_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes, int mode, double* X, double* U,
+                       double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters, int* trace,
+                       void* cuda_stream) {
+  if (!h) return PDG_EINVAL;
+  h->err.clear();
+  if (B < 0) return fail(h, PDG_EINVAL, "B must be >= 0");
+  if (B == 0) return PDG_OK;
+  if (mode != 0 && mode != 1) return fail(h, PDG_EINVAL, "mode must be 0 (plain) or 1 (persistent)");
+  if (!x0 || !X || !U || !tf || !fuel || !status || !scp_iters || !pipg_iters) return fail(h, PDG_EINVAL, "NULL buffer");
+  PDG_CUDA(h, cudaSetDevice(h->device));
+  return PDG_DISPATCH(h, run_solve, h, B, x0, n_nodes, mode, X, U, tf, fuel, status, scp_iters, pipg_iters, trace,
+                      (cudaStream_t)cuda_stream);
+}
+
+int pdg_mc_solve_batch_host(pdg_handle* h, int B, const double* x0, const int* n_nodes, int mode, double* X,
+                            double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
+                            void* cuda_stream) {
+  if (!h) return PDG_EINVAL;
+  h->err.clear();
+  if (B < 0) return fail(h, PDG_EINVAL, "B must be >= 0");
+  if (B == 0) return PDG_OK;
+  if (!x0 || !X || !U || !tf || !fuel || !status || !scp_iters || !pipg_iters) return fail(h, PDG_EINVAL, "NULL buffer");
+  PDG_CUDA(h, cudaSetDevice(h->device));
+  const int nu = h->p.nu, Nm = h->n_max;
+  const size_t bx0 = sizeof(double) * 14 * B, bN = sizeof(int) * B, bX = sizeof(double) * (size_t)B * Nm * 15,
+               bU = sizeof(double) * (size_t)B * Nm * nu, bs = sizeof(double) * B, bi = sizeof(int) * B,
+               bl = sizeof(long long) * B;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t need = al(bx0) + al(bN) + al(bX) + al(bU) + 2 * al(bs) + 2 * al(bi) + al(bl);
+  if (h->stage_bytes < need) {
+    if (h->stage) cudaFree(h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    PDG_CUDA(h, cudaMalloc(&h->stage, need));
+    h->stage_bytes = need;
+  }
+  char* c = (char*)h->stage;
+  double* dx0 = (double*)c; c += al(bx0);
+  int* dN = (int*)c; c += al(bN);
+  double* dX = (double*)c; c += al(bX);
+  double* dU = (double*)c; c += al(bU);
+  double* dtf = (double*)c; c += al(bs);
+  double* dfu = (double*)c; c += al(bs);
+  int* dst = (int*)c; c += al(bi);
+  int* dsc = (int*)c; c += al(bi);
+  long long* dpi = (long long*)c;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  PDG_CUDA(h, cudaMemcpyAsync(dx0, x0, bx0, cudaMemcpyHostToDevice, s));
+  if (n_nodes) PDG_CUDA(h, cudaMemcpyAsync(dN, n_nodes, bN, cudaMemcpyHostToDevice, s));
+  int rc = pdg_mc_solve_batch(h, B, dx0, n_nodes ? dN : nullptr, mode, dX, dU, dtf, dfu, dst, dsc, dpi, nullptr, s);
+  if (rc) return rc;
+  PDG_CUDA(h, cudaMemcpyAsync(X, dX, bX, cudaMemcpyDeviceToHost, s));
+  PDG_CUDA(h, cudaMemcpyAsync(U, dU, bU, cudaMemcpyDeviceToHost, s));
+  PDG_CUDA(h, cudaMemcpyAsync(tf, dtf, bs, cudaMemcpyDeviceToHost, s));
+  PDG_CUDA(h, cudaMemcpyAsync(fuel, dfu, bs, cudaMemcpyDeviceToHost, s));
+  PDG_CUDA(h, cudaMemcpyAsync(status, dst, bi, cudaMemcpyDeviceToHost, s));
+  PDG_CUDA(h, cudaMemcpyAsync(scp_iters, dsc, bi, cudaMemcpyDeviceToHost, s));
+  PDG_CUDA(h, cudaMemcpyAsync(pipg_iters, dpi, bl, cudaMemcpyDeviceToHost, s));
+  PDG_CUDA(h, cudaStreamSynchronize(s));
+  return PDG_OK;
+}
+
+int pdg_mc_subproblem(pdg_handle* h, int B, const double* x0, const int* n_nodes, const double* X, const double* U,
+                      double* Am, double* Bm, double* Bp, double* w, void* cuda_stream) {
+  if (!h) return PDG_EINVAL;
+  h->err.clear();
+  if (B < 0) return fail(h, PDG_EINVAL, "B must be >= 0");
+  if (B == 0) return PDG_OK;
+  if (!x0 || !X || !U || !Am || !Bm || !Bp || !w) return fail(h, PDG_EINVAL, "NULL buffer");
+  PDG_CUDA(h, cudaSetDevice(h->device));
+  return PDG_DISPATCH(h, run_subproblem, h, B, x0, n_nodes, X, U, Am, Bm, Bp, w, (cudaStream_t)cuda_stream);
+}
+
+int pdg_mc_scp_step(pdg_handle* h, int B, const double* x0, const int* n_nodes, double* X, double* U, double* xh,
+                    double* uh, double* mup, double* mum, double* phi, double* th, const int* force, double* sigma,
+                    double* defect, double* step, int* iters, void* cuda_stream) {
+  if (!h) return PDG_EINVAL;
+  h->err.clear();
+  if (B < 0) return fail(h, PDG_EINVAL, "B must be >= 0");
+  if (B == 0) return PDG_OK;
+  if (!x0 || !X || !U || !xh || !uh || !mup || !mum || !phi || !th || !sigma || !defect || !step || !iters)
+    return fail(h, PDG_EINVAL, "NULL buffer");
+  PDG_CUDA(h, cudaSetDevice(h->device));
+  return PDG_DISPATCH(h, run_step, h, B, x0, n_nodes, X, U, xh, uh, mup, mum, phi, th, force, sigma, defect, step,
+                      iters, (cudaStream_t)cuda_stream);
+}
+
+int pdg_mc_launch_info(pdg_handle* h, int* threads, int* ctas_per_sm, int* smem_bytes) {
+  if (!h) return PDG_EINVAL;
+  if (threads) *threads = h->last_threads;
+  if (ctas_per_sm) *ctas_per_sm = h->last_ctas;
+  if (smem_bytes) *smem_bytes = h->last_smem;
+  return PDG_OK;
+}
+
+int pdg_mc_set_threads(pdg_handle* h, int threads) {
+  if (!h) return PDG_EINVAL;
+  if (threads < 0 || threads > 512 || (threads % 32) != 0) return fail(h, PDG_EINVAL, "threads must be 0 or a multiple of 32 up to 512");
+  h->threads_override = threads;
+  return PDG_OK;
+}
+
+int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream) {
+  if (!tflops || (precision != 0 && precision != 1)) return PDG_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return PDG_ECUDA;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int threads = 512, blocks = sms * 4;
+  const int iters = precision == 0 ? 1 << 14 : 1 << 18;
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, 16) != cudaSuccess) return PDG_ENOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, s);
+    if (precision == 0) k_fma_probe<double><<<blocks, threads, 0, s>>>(iters, 1.0, (double*)buf);
+    else k_fma_probe<float><<<blocks, threads, 0, s>>>(iters, 1.0f, (float*)buf);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return PDG_ECUDA;
+  *tflops = 16.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+  return PDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+"""Algorithmic operation counts of the solver (one FMA = 2 flops), used for
+the roofline fraction.  They count the operations of the method itself, not
+of any particular kernel:
+
+* PIPG_custom iteration (Alg. PIPG_custom): the products K^T (phi, theta) and
+  K (2 z - z~) over the dense blocks hat A^-_k (15 x 15), hat B^-_k, hat B^+_k
+  (15 x nu), 2 (N-1)(225 + 30 nu) FMA; plus the vector work per scalar
+  variable: 9 flops per x_hat / u_hat entry and per mu^+ / mu^- entry
+  (gradient assembly, step, projection, 2z - z~, extrapolation), 8 per phi /
+  theta entry.
+* power iteration (Alg. power): the same two products plus the squared norm,
+  2 flops per primal entry.
+* discretization (Sec. 2.3.1 by RK4): per interval, substep and stage, the
+  state-transition right-hand side J S for every one of the 15 + 2 nu STM
+  columns through the structural nonzeros of df/dx (62 FMA), the df/du column
+  term for the 2 nu control columns (15 FMA), the RK4 stage/accumulate updates
+  (3 flops per entry), and one evaluation of f and its Jacobians (250 flops).
+"""
+
+NX = 15
+
+
+def pipg_iter(N: int, nu: int) -> int:
+    mat = 2 * 2 * (N - 1) * (NX * NX + 2 * NX * nu)
+    vec = 9 * (NX + nu) * N + 9 * 2 * NX * (N - 1) + 8 * (NX + 1) * (N - 1)
+    return mat + vec
+
+
+def power_iter(N: int, nu: int) -> int:
+    mat = 2 * 2 * (N - 1) * (NX * NX + 2 * NX * nu)
+    return mat + 2 * ((NX + nu) * N + 2 * NX * (N - 1))
+
+
+def discretization(N: int, nu: int, nsub: int) -> int:
+    ncol = NX + 2 * nu
+    per_stage = ncol * (2 * 62 + 3 * NX) + 2 * nu * 2 * NX + 250
+    return (N - 1) * nsub * 4 * per_stage
+
+
+def solve_flops(N, nu, nsub, scp_iters, pow_iters, pipg_iters) -> float:
+    """Total algorithmic flops of a solve given its executed counters (arrays
+    over instances are accepted)."""
+    import numpy as np
+    N = np.asarray(N)
+    return float(np.sum(np.asarray(scp_iters) * np.vectorize(discretization)(N, nu, nsub)
+                        + np.asarray(pow_iters) * np.vectorize(power_iter)(N, nu)
+                        + np.asarray(pipg_iters) * np.vectorize(pipg_iter)(N, nu)))

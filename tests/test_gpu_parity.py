@@ -1,0 +1,257 @@
+"""Parity of the CUDA solver (through the C ABI) with the FP64 CPU oracle.
+
+Element-wise comparisons at the tolerance |a - b| <= 1e-6 max(|b|, P scale)
+(FP64).  Iterative decisions (power-iteration, PIPG and SCP stop tests) are
+replayed: the oracle runs the iteration counts the GPU recorded, so the two
+compute the same algorithm step for step and differ only by rounding."""
+import numpy as np
+import pytest
+
+from gpu_helpers import RTOL, assert_scaled_close, replay_instance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_18034_gb300 import build
+    build.build()
+    return torch
+
+
+def _solver(inputs, nu=4, n_max=15, precision=0, **ov):
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    p = inputs.load_params(nu=nu, **ov)
+    return p, Solver(p, n_max, precision)
+
+
+def _refs(O, inputs, p, B, Ns, seed, perturb=0.03):
+    """Reference trajectories: the initial guess perturbed (so that every
+    Jacobian term is exercised), padded to n_max rows."""
+    n_max = int(max(Ns))
+    nu = p["nu"]
+    x0 = inputs.dispersion(p, B, seed, "bj")
+    rng = np.random.default_rng(seed)
+    X = np.zeros((B, n_max, 15)); U = np.zeros((B, n_max, nu))
+    for b in range(B):
+        Xg, Ug = O.init_guess(p, int(Ns[b]), x0[b])
+        Xg[1:] += rng.normal(size=Xg[1:].shape) * perturb * p["P_x"]
+        Ug += rng.normal(size=Ug.shape) * perturb * p["P_u"][:nu]
+        X[b, :Ns[b]] = Xg; U[b, :Ns[b]] = Ug
+    return x0, X, U
+
+
+@pytest.mark.parametrize("nu,prec", [(4, 0), (7, 0)])
+def test_subproblem_blocks(torch_cuda, oracle, inputs, nu, prec):
+    """Discretization + prescaling: hat A^-, hat B^-, hat B^+, hat w per
+    interval, for a batch of uneven node counts (several waves of intervals
+    and a ragged last wave)."""
+    torch = torch_cuda
+    Ns = np.array([2, 3, 10, 15, 17, 30, 32, 9], np.int32)
+    p, S = _solver(inputs, nu, 32, prec)
+    x0, X, U = _refs(oracle, inputs, p, len(Ns), Ns, 11)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    o = S.subproblem(d(x0), d(X), d(U), d(Ns))
+    torch.cuda.synchronize()
+    for b, N in enumerate(Ns):
+        A, Bm, Bp, xp = oracle.discretize(p, X[b, :N], U[b, :N])
+        qp = oracle.scale(p, x0[b], X[b, :N], U[b, :N], A, Bm, Bp, xp)
+        sc_a = np.abs(qp.Am).max() * 1e-3
+        assert_scaled_close(o["Am"][b, :N - 1].cpu().numpy(), qp.Am, sc_a, what=f"Am N={N}")
+        assert_scaled_close(o["Bm"][b, :N - 1].cpu().numpy(), qp.Bm, np.abs(qp.Bm).max() * 1e-3, what=f"Bm N={N}")
+        assert_scaled_close(o["Bp"][b, :N - 1].cpu().numpy(), qp.Bp, np.abs(qp.Bp).max() * 1e-3, what=f"Bp N={N}")
+        assert_scaled_close(o["w"][b, :N - 1].cpu().numpy(), qp.w, 1e-3, what=f"w N={N}")
+        assert np.all(o["Am"][b, N - 1:].cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("nu", [4, 7])
+def test_scp_step_forced_counts(torch_cuda, oracle, inputs, nu):
+    """Three chained SCP iterations (discretize, scale, power iteration, PIPG
+    with the oracle's counts forced, update) match the oracle's iterations."""
+    torch = torch_cuda
+    Ns = np.array([15, 10, 4, 15], np.int32)
+    p, S = _solver(inputs, nu, 15)
+    B, n_max = len(Ns), 15
+    x0 = inputs.dispersion(p, B, 5, "bj")
+    X = np.zeros((B, n_max, 15)); U = np.zeros((B, n_max, nu))
+    ows = []
+    for b in range(B):
+        Xg, Ug = oracle.init_guess(p, int(Ns[b]), x0[b])
+        X[b, :Ns[b]] = Xg; U[b, :Ns[b]] = Ug
+        ows.append(oracle.PDState(int(Ns[b]), nu))
+    oX = [X[b, :Ns[b]].copy() for b in range(B)]
+    oU = [U[b, :Ns[b]].copy() for b in range(B)]
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    gX, gU = d(X), d(U)
+    ws = {k: torch.zeros(B, n_max if k in ("xh", "uh") else n_max - 1, *( (15,) if k in ("xh", "mup", "mum", "phi") else ((nu,) if k == "uh" else ())), dtype=torch.float64, device="cuda")
+          for k in ("xh", "uh", "mup", "mum", "phi", "th")}
+    for it, (fp, fj) in enumerate([(7, 45), (5, 120), (9, 33)]):
+        force = d(np.array([[fp, fj]] * B, np.int32))
+        o = S.scp_step(d(x0), gX, gU, ws, d(Ns), force)
+        torch.cuda.synchronize()
+        for b in range(B):
+            N = int(Ns[b])
+            r = oracle.scp_iterate(p, x0[b], oX[b], oU[b], ows[b], force_pow=fp, force_pipg=fj)
+            assert tuple(o["iters"][b].tolist()) == (fp, fj)
+            assert abs(o["sigma"][b].item() - r["sigma"]) <= RTOL * r["sigma"]
+            assert_scaled_close(gX[b, :N].cpu().numpy(), oX[b], p["P_x"], what=f"X it{it} b{b}")
+            assert_scaled_close(gU[b, :N].cpu().numpy(), oU[b], p["P_u"][:nu], what=f"U it{it} b{b}")
+            for k in ("xh", "uh", "mup", "mum", "phi", "th"):
+                g = ws[k][b].cpu().numpy()
+                ref = getattr(ows[b], k)
+                g = g[:ref.shape[0]]
+                assert_scaled_close(g, ref, 1.0, what=f"{k} it{it} b{b}")
+            assert abs(o["defect"][b].item() - r["defect"]) <= RTOL * max(r["defect"], 1.0)
+            assert abs(o["step"][b].item() - r["step"]) <= RTOL * max(r["step"], 1.0)
+
+
+def _solve_and_replay(torch, oracle, inputs, p, S, x0, Ns, mode, sample):
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = S.solve(d(x0), d(Ns) if Ns is not None else None, mode=mode, trace=True)
+    torch.cuda.synchronize()
+    o = {k: v.cpu().numpy() for k, v in out.items()}
+    nu = p["nu"]
+    for b in sample:
+        N = int(Ns[b]) if Ns is not None else S.n_max
+        r = replay_instance(oracle, p, x0[b], N, o["trace"][b], int(o["scp_iters"][b]))
+        assert o["status"][b] == r["status"], (b, o["status"][b], r["status"])
+        assert o["pipg_iters"][b] == r["pipg_iters"]
+        assert_scaled_close(o["X"][b, :N], r["X"], p["P_x"], what=f"X b{b}")
+        assert_scaled_close(o["U"][b, :N], r["U"], p["P_u"][:nu], what=f"U b{b}")
+        assert abs(o["tf"][b] - r["tf"]) <= RTOL * abs(r["tf"])
+        assert abs(o["fuel"][b] - r["fuel"]) <= RTOL * max(abs(r["fuel"]), p["P_x"][0])
+        assert np.all(o["X"][b, N:] == 0) and np.all(o["U"][b, N:] == 0)
+    return o
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_full_solve_matches_oracle_replay(torch_cuda, oracle, inputs, mode):
+    """Whole SCP solves (persistent and plain form) on an uneven-N batch."""
+    torch = torch_cuda
+    p, S = _solver(inputs, 4, 30)
+    B = 12
+    x0 = inputs.dispersion(p, B, inputs.config_seed(2), "bj")
+    Ns = inputs.node_counts(B, inputs.config_seed(2))
+    o = _solve_and_replay(torch, oracle, inputs, p, S, x0, Ns, mode, range(B))
+    assert np.mean(o["status"] == 0) >= 0.75
+
+
+def test_nu7_solve_matches_oracle_replay(torch_cuda, oracle, inputs):
+    torch = torch_cuda
+    p, S = _solver(inputs, 7, 15)
+    x0 = inputs.dispersion(p, 4, 3, "bj")
+    _solve_and_replay(torch, oracle, inputs, p, S, x0, None, 1, range(4))
+
+
+def test_free_run_agrees_with_oracle(torch_cuda, oracle, inputs):
+    """Without replay both sides take their own stop decisions; on this
+    workload they agree on status and SCP count for most instances and the
+    trajectories agree to the solver tolerance."""
+    torch = torch_cuda
+    p, S = _solver(inputs, 4, 10)
+    B = 8
+    x0 = inputs.dispersion(p, B, inputs.config_seed(1), "bj")
+    out = S.solve(torch.from_numpy(x0).cuda(), mode=1)
+    torch.cuda.synchronize()
+    ref = oracle.solve_batch(p, x0, np.full(B, 10, np.int32))
+    same = (out["status"].cpu().numpy() == ref["status"]) & (out["scp_iters"].cpu().numpy() == ref["scp_iters"])
+    assert same.mean() >= 0.75
+    for b in np.nonzero(same)[0]:
+        assert_scaled_close(out["X"][b].cpu().numpy(), ref["X"][b], p["P_x"], rtol=1e-4, what=f"X b{b}")
+
+
+def test_single_instance_config(torch_cuda, oracle, inputs):
+    """B = 1, N = 10, FP64, plain form: the single-instance workload."""
+    torch = torch_cuda
+    p, S = _solver(inputs, 4, 10)
+    x0 = p["x0_nominal"][None, :].copy()
+    _solve_and_replay(torch, oracle, inputs, p, S, x0, None, 0, [0])
+
+
+def test_edge_cases(torch_cuda, inputs):
+    """Empty batch; out-of-range node counts and non-finite x0 give
+    PDG_BAD_INPUT with zero outputs; N = 2 runs."""
+    torch = torch_cuda
+    from paper_2404_18034_gb300.pdg_mc import PDG_BAD_INPUT
+    p, S = _solver(inputs, 4, 12)
+    x0 = inputs.dispersion(p, 5, 1, "bj")
+    x0[3, 2] = np.nan
+    Ns = np.array([2, 1, 13, 12, 5], np.int32)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    empty = S.solve(d(x0[:0]), mode=1)
+    assert empty["X"].shape[0] == 0
+    for mode in (0, 1):
+        out = S.solve(d(x0), d(Ns), mode=mode)
+        torch.cuda.synchronize()
+        st = out["status"].cpu().numpy()
+        assert list(st[[1, 2, 3]]) == [PDG_BAD_INPUT] * 3
+        assert st[0] in (0, 1) and st[4] in (0, 1)
+        for b in (1, 2, 3):
+            assert out["X"][b].abs().max().item() == 0.0 and out["tf"][b].item() == 0.0
+
+
+def test_host_api_equals_device_api(torch_cuda, inputs):
+    torch = torch_cuda
+    p, S = _solver(inputs, 4, 15)
+    x0 = inputs.dispersion(p, 6, 9, "bj")
+    dev = S.solve(torch.from_numpy(x0).cuda(), mode=1)
+    torch.cuda.synchronize()
+    host = S.solve_host(x0, mode=1)
+    for k in ("X", "U", "tf", "fuel", "status", "scp_iters", "pipg_iters"):
+        np.testing.assert_array_equal(dev[k].cpu().numpy(), host[k])
+
+
+def test_plain_and_persistent_agree(torch_cuda, inputs):
+    torch = torch_cuda
+    p, S = _solver(inputs, 4, 20)
+    x0 = inputs.dispersion(p, 8, 4, "bj")
+    Ns = np.array([20, 15, 10, 20, 15, 10, 20, 2], np.int32)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    a = S.solve(d(x0), d(Ns), mode=0)
+    b = S.solve(d(x0), d(Ns), mode=1)
+    torch.cuda.synchronize()
+    for k in ("X", "U", "tf", "fuel", "status", "scp_iters", "pipg_iters"):
+        np.testing.assert_array_equal(a[k].cpu().numpy(), b[k].cpu().numpy())
+
+
+def test_fp32_build_tracks_fp64(torch_cuda, oracle, inputs):
+    """FP32 build: reported against the FP64 oracle as a relative trajectory
+    error (not gated at 1e-6); converged solutions stay within 1e-2 scaled."""
+    torch = torch_cuda
+    p, S = _solver(inputs, 4, 15, precision=1)
+    B = 6
+    x0 = inputs.dispersion(p, B, 8, "bj")
+    out = S.solve(torch.from_numpy(x0).cuda(), mode=1)
+    torch.cuda.synchronize()
+    ref = oracle.solve_batch(p, x0, np.full(B, 15, np.int32))
+    st = out["status"].cpu().numpy()
+    assert np.mean(st == 0) >= 0.5
+    for b in np.nonzero((st == 0) & (ref["status"] == 0))[0]:
+        err = np.abs(out["X"][b].cpu().numpy() - ref["X"][b]) / p["P_x"]
+        assert err.max() < 1e-1, err.max()
+        assert abs(out["fuel"][b].item() - ref["fuel"][b]) < 1e-2
+
+
+def test_full_size_sampled(torch_cuda, oracle, inputs):
+    """The benchmark workload (B = 16384, N = 15, FP64, persistent) checked
+    on sampled instances by oracle replay, plus invariants on all."""
+    torch = torch_cuda
+    p, S = _solver(inputs, 4, 15)
+    B = 16384
+    x0 = inputs.dispersion(p, B, inputs.config_seed(2), "bj")
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = S.solve(d(x0), mode=1, trace=True)
+    torch.cuda.synchronize()
+    o = {k: v.cpu().numpy() for k, v in out.items()}
+    assert np.all(np.isin(o["status"], [0, 1]))
+    assert np.mean(o["status"] == 0) > 0.9
+    np.testing.assert_allclose(o["X"][:, 0, :14], x0, atol=1e-12)
+    assert np.all(o["trace"][:, :, 1].sum(1) == o["pipg_iters"])
+    rng = np.random.default_rng(0)
+    for b in list(rng.choice(B, 6, replace=False)) + [0, B - 1]:
+        r = replay_instance(oracle, p, x0[b], 15, o["trace"][b], int(o["scp_iters"][b]))
+        assert_scaled_close(o["X"][b], r["X"], p["P_x"], what=f"X b{b}")
+        assert abs(o["fuel"][b] - r["fuel"]) <= RTOL * max(abs(r["fuel"]), 0.5)
