@@ -11,7 +11,7 @@ def assert_scaled_close(a, b, scale, rtol=RTOL, what=""):
     b = np.asarray(b, np.float64)
     tol = rtol * np.maximum(np.abs(b), scale)
     err = np.abs(a - b)
-    bad = err > tol
+    bad = ~(err <= tol)  # NaN anywhere counts as a mismatch
     assert not bad.any(), f"{what}: max err {err.max():.3e}, worst ratio {(err / tol).max():.3e} at {np.argwhere(bad)[:5]}"
 
 

@@ -119,6 +119,8 @@ def _solve_and_replay(torch, oracle, inputs, p, S, x0, Ns, mode, sample):
         r = replay_instance(oracle, p, x0[b], N, o["trace"][b], int(o["scp_iters"][b]))
         assert o["status"][b] == r["status"], (b, o["status"][b], r["status"])
         assert o["pipg_iters"][b] == r["pipg_iters"]
+        if r["status"] == 2:  # non-finite on both sides: the outputs carry no values to compare
+            continue
         assert_scaled_close(o["X"][b, :N], r["X"], p["P_x"], what=f"X b{b}")
         assert_scaled_close(o["U"][b, :N], r["U"], p["P_u"][:nu], what=f"U b{b}")
         assert abs(o["tf"][b] - r["tf"]) <= RTOL * abs(r["tf"])
