@@ -40,16 +40,26 @@ struct Lay {
   int xt, ut, nup, num, vph, vth, dx, du, dmu, stage, red, total;
 };
 
-// stage buffer of one interval: compact A (40) then dense B (15 x nu)
+// stage buffer of one interval: compact A (40), dense B (15 x nu), then the
+// evaluator's RK4 state of x: base P, accumulator, stage input (15 each)
 constexpr int SA_A = 40;
+
+// Intervals per discretization wave: warp 0 evaluates the model of up to 32
+// intervals, the remaining warps hold one STM column per thread.
+__host__ __device__ inline int waves_ipw(int threads, int nu) {
+  const int ncol = NX + 2 * nu;
+  const int w = (threads - 32) / ncol;
+  return w > 32 ? 32 : w;
+}
+
+__host__ __device__ inline int round32(int x) { return (x + 31) & ~31; }
 
 __host__ __device__ inline Lay make_lay(int N, int nu, int threads) {
   Lay L;
   L.N = N;
   L.nu = nu;
-  const int ncol = NX + 2 * nu;
-  L.ipw = threads / (ncol + 1);
-  L.sa = SA_A + NX * nu;
+  L.ipw = waves_ipw(threads, nu);
+  L.sa = SA_A + NX * nu + 3 * NX;
   int o = 0;
   L.sc = o; o += 8;
   L.x0 = o; o += 16;

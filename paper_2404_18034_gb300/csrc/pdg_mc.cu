@@ -485,16 +485,11 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
 }
 
 
-// Threads per CTA: enough for one discretization wave of the largest instance
-// (capped at 512) and at least two PIPG dual rows per thread.
+// Threads per CTA: one thread per dual row of the largest instance (whole
+// warps) plus the warp of CTCS rows, within [128, 512].
 static int pick_threads(const pdg_handle* h) {
   if (h->threads_override > 0) return h->threads_override;
-  const int nu = h->p.nu, N = h->n_max;
-  const int per = 15 + 2 * nu + 1;
-  int t = (N - 1) * per;
-  const int dual = (N - 1) * 16;
-  if (t < dual) t = dual;
-  t = (t + 31) / 32 * 32;
+  int t = round32((h->n_max - 1) * 15) + 32;
   if (t > 512) t = 512;
   if (t < 128) t = 128;
   return t;

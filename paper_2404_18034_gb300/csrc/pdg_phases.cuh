@@ -7,6 +7,10 @@
 
 namespace pdg {
 
+// max(0, x) by a sign-bit test, kept off the FP64 pipe.
+__device__ __forceinline__ double max0(double x) { return __double_as_longlong(x) < 0 ? 0.0 : x; }
+__device__ __forceinline__ float max0(float x) { return __float_as_int(x) < 0 ? 0.0f : x; }
+
 // Initial guess (the paper asks for "an appropriate" one; Sec. 5): straight
 // lines in r, v, w from x0 to z_f, normalized linear interpolation of q, mass
 // from m_wet to (m_wet + m_dry)/2, y = 0, hover thrust m|g| along body x,
@@ -54,14 +58,14 @@ __device__ void phase_init_guess(const DParams& P, const Lay& L, R* sm) {
 // Sec. 2.3.1 + 2.3.2: integrate, on every interval, the joint IVP of x and its
 // state-transition matrices with RK4 (nsub substeps, FOH controls), then write
 // the prescaled blocks hat A^-_k, hat B^-_k, hat B^+_k, hat w_k.  Thread
-// mapping: per interval, one thread per STM column (15 + 2 NU of them, each
-// column held in registers) plus one thread integrating x and evaluating the
-// compact Jacobians at each RK4 stage.  Intervals are processed in waves of
-// L.ipw.  Returns max_k |hat w_k|_inf (the scaled defect) on every thread.
+// mapping: lane l of warp 0 integrates x on interval k0 + l and evaluates the
+// compact Jacobians at each RK4 stage (its RK4 state lives in the interval's
+// stage buffer); every thread of warps 1.. holds one STM column (15 + 2 NU per
+// interval) in registers.  Intervals are processed in waves of L.ipw.
+// Returns max_k |hat w_k|_inf (the scaled defect) on every thread.
 template <typename R, int NU>
 __device__ R phase_discretize(const DParams& P, const Lay& L, R* sm) {
   constexpr int NCOL = NX + 2 * NU;
-  constexpr int PER = NCOL + 1;
   const int N = L.N;
   const R* Xb = sm + L.Xb;
   const R* Ub = sm + L.Ub;
@@ -72,50 +76,60 @@ __device__ R phase_discretize(const DParams& P, const Lay& L, R* sm) {
   const int nsub = P.nsub;
   const R h = R(1) / (R(N - 1) * R(nsub));
   const R h2 = R(0.5) * h, h6 = h / R(6);
-  const int my = threadIdx.x / PER;
-  const int c = threadIdx.x - my * PER;
+  const bool evaluator = threadIdx.x < 32;
+  const int ct = threadIdx.x - 32;
+  const int il = evaluator ? threadIdx.x : ct / NCOL;
+  const int c = evaluator ? -1 : ct - il * NCOL;
+  const int cu = c >= NX ? (c - NX) % NU : -1;
+  const bool minus = c >= NX && (c - NX) < NU;
   R dmax = 0;
   for (int k0 = 0; k0 < N - 1; k0 += L.ipw) {
-    const int k = k0 + my;
-    const bool active = my < L.ipw && k < N - 1;
-    R* st = sm + L.stage + (my < L.ipw ? my : 0) * L.sa;
-    R Pv[NX], Sv[NX], Ac[NX], uk[NU], uk1[NU];
-    int cu = -1;
-    bool minus = false;
+    const int k = k0 + il;
+    const bool active = il < L.ipw && k < N - 1;
+    R* st = sm + L.stage + (active ? il : 0) * L.sa;
+    R* xP = st + SA_A + NX * NU;
+    R* xA = xP + NX;
+    R* xS = xA + NX;
+    R Pv[NX], Sv[NX], Ac[NX];
     if (active) {
-      if (c == NCOL) {
+      if (evaluator) {
 #pragma unroll
-        for (int i = 0; i < NX; ++i) Pv[i] = Xb[k * NX + i];
-#pragma unroll
-        for (int i = 0; i < NU; ++i) { uk[i] = Ub[k * NU + i]; uk1[i] = Ub[(k + 1) * NU + i]; }
+        for (int i = 0; i < NX; ++i) { xP[i] = Xb[k * NX + i]; xS[i] = Xb[k * NX + i]; }
       } else {
 #pragma unroll
-        for (int i = 0; i < NX; ++i) Pv[i] = (c == i) ? R(1) : R(0);
-        if (c >= NX) {
-          cu = (c - NX) % NU;
-          minus = (c - NX) < NU;
-        }
+        for (int i = 0; i < NX; ++i) { Pv[i] = (c == i) ? R(1) : R(0); Sv[i] = Pv[i]; }
       }
-#pragma unroll
-      for (int i = 0; i < NX; ++i) Sv[i] = Pv[i];
     }
     for (int n = 0; n < nsub; ++n) {
 #pragma unroll 1
       for (int sgi = 0; sgi < 4; ++sgi) {
         const R lp = (R(n) + (sgi == 0 ? R(0) : (sgi == 3 ? R(1) : R(0.5)))) / R(nsub);
-        R d[NX];
-        if (active && c == NCOL) {
-          R u[NU];
+        if (active && evaluator) {
+          R u[NU], x[NX], d[NX];
 #pragma unroll
-          for (int i = 0; i < NU; ++i) u[i] = (R(1) - lp) * uk[i] + lp * uk1[i];
-          model_eval<R, NU>(P, Sv, u, d, st, st + SA_A);
+          for (int i = 0; i < NU; ++i) u[i] = (R(1) - lp) * Ub[k * NU + i] + lp * Ub[(k + 1) * NU + i];
+#pragma unroll
+          for (int i = 0; i < NX; ++i) x[i] = xS[i];
+          model_eval<R, NU>(P, x, u, d, st, st + SA_A);
+          if (sgi == 0) {
+#pragma unroll
+            for (int i = 0; i < NX; ++i) { xA[i] = d[i]; xS[i] = xP[i] + h2 * d[i]; }
+          } else if (sgi == 1) {
+#pragma unroll
+            for (int i = 0; i < NX; ++i) { xA[i] += R(2) * d[i]; xS[i] = xP[i] + h2 * d[i]; }
+          } else if (sgi == 2) {
+#pragma unroll
+            for (int i = 0; i < NX; ++i) { xA[i] += R(2) * d[i]; xS[i] = xP[i] + h * d[i]; }
+          } else {
+#pragma unroll
+            for (int i = 0; i < NX; ++i) { const R v = xP[i] + h6 * (xA[i] + d[i]); xP[i] = v; xS[i] = v; }
+          }
         }
         __syncthreads();
-        if (active && c < NCOL) {
+        if (active && !evaluator) {
+          R d[NX];
           const R lam = minus ? (R(1) - lp) : lp;
           model_jvp<R, NU>(st, st + SA_A, Sv, cu, lam, d);
-        }
-        if (active) {
           if (sgi == 0) {
 #pragma unroll
             for (int i = 0; i < NX; ++i) { Ac[i] = d[i]; Sv[i] = Pv[i] + h2 * d[i]; }
@@ -134,10 +148,10 @@ __device__ R phase_discretize(const DParams& P, const Lay& L, R* sm) {
       }
     }
     if (active) {
-      if (c == NCOL) {
+      if (evaluator) {
 #pragma unroll
         for (int i = 0; i < NX; ++i) {
-          const R wi = (Pv[i] - Xb[(k + 1) * NX + i]) * R(P.Pxinv[i]);
+          const R wi = (xP[i] - Xb[(k + 1) * NX + i]) * R(P.Pxinv[i]);
           w[k * NX + i] = wi;
           dmax = rmax(dmax, fabs(wi));
         }
@@ -188,11 +202,13 @@ __device__ void phase_scale_extra(const DParams& P, const Lay& L, R* sm) {
 // Alg. power on K = [G; H_y] (readings: v_k is theta_k; sigma* accumulates from
 // sigma*; start from the warm-start primal, or all ones when it is zero).  The
 // iterate (x, u, mu+, mu-) lives in the xt/ut/nup/num scratch, (phi, theta) in
-// vph/vth.  Returns the buffered sigma; *iters the iterations run.
+// vph/vth.  Task ranges are padded to whole warps so that every warp runs one
+// kind of task.  Returns the buffered sigma; *iters the iterations run.
 template <typename R, int NU>
 __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* iters) {
   const int N = L.N, T = blockDim.x, tid = threadIdx.x;
   const int nx = N * NX, nuu = N * NU, nm = (N - 1) * NX;
+  const int PX = round32(nx), PU = round32(nuu), PM = round32(nm);
   const R* Am = sm + L.Am;
   const R* Bm = sm + L.Bm;
   const R* Bp = sm + L.Bp;
@@ -231,67 +247,76 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
   for (j = 1; j <= jmax; ++j) {
     const R isig = R(1) / sig;
     // phi = K z / sigma
-    for (int t = tid; t < nm + (N - 1); t += T) {
-      if (t < nm) {
-        const int k = t / NX, i = t - NX * k;
-        const R* a = Am + (k * NX + i) * NX;
-        const R* xk = px + k * NX;
-        R r = pp[t] - pn[t] - px[(k + 1) * NX + i];
+    for (int t = tid; t < PM + 32; t += T) {
+      if (t < PM) {
+        if (t < nm) {
+          const int k = t / NX, i = t - NX * k;
+          const R* a = Am + (k * NX + i) * NX;
+          const R* xk = px + k * NX;
+          R r = pp[t] - pn[t] - px[(k + 1) * NX + i];
 #pragma unroll
-        for (int cc = 0; cc < NX; ++cc) r += a[cc] * xk[cc];
-        const R* bm = Bm + (k * NX + i) * NU;
-        const R* bp = Bp + (k * NX + i) * NU;
+          for (int cc = 0; cc < NX; ++cc) r += a[cc] * xk[cc];
+          const R* bm = Bm + (k * NX + i) * NU;
+          const R* bp = Bp + (k * NX + i) * NU;
 #pragma unroll
-        for (int cc = 0; cc < NU; ++cc) r += bm[cc] * pu[k * NU + cc] + bp[cc] * pu[(k + 1) * NU + cc];
-        ph[t] = r * isig;
+          for (int cc = 0; cc < NU; ++cc) r += bm[cc] * pu[k * NU + cc] + bp[cc] * pu[(k + 1) * NU + cc];
+          ph[t] = r * isig;
+        }
       } else {
-        const int k = t - nm;
-        pt[k] = (px[(k + 1) * NX + IY] - px[k * NX + IY]) * isig;
+        const int k = t - PM;
+        if (k < N - 1) pt[k] = (px[(k + 1) * NX + IY] - px[k * NX + IY]) * isig;
       }
     }
     __syncthreads();
     // z = K^T (phi, theta)
     R s2 = 0;
-    for (int t = tid; t < nx + nuu + nm; t += T) {
-      if (t < nx) {
-        const int k = t / NX, i = t - NX * k;
-        R g = 0;
-        if (k < N - 1) {
-          const R* a = Am + k * NX * NX + i;
-          const R* f = ph + k * NX;
+    for (int t = tid; t < PX + PU + PM; t += T) {
+      if (t < PX) {
+        if (t < nx) {
+          const int k = t / NX, i = t - NX * k;
+          R g = 0;
+          if (k < N - 1) {
+            const R* a = Am + k * NX * NX + i;
+            const R* f = ph + k * NX;
 #pragma unroll
-          for (int r = 0; r < NX; ++r) g += a[r * NX] * f[r];
-          if (i == IY) g -= pt[k];
+            for (int r = 0; r < NX; ++r) g += a[r * NX] * f[r];
+            if (i == IY) g -= pt[k];
+          }
+          if (k > 0) {
+            g -= ph[(k - 1) * NX + i];
+            if (i == IY) g += pt[k - 1];
+          }
+          px[t] = g;
+          s2 += g * g;
         }
-        if (k > 0) {
-          g -= ph[(k - 1) * NX + i];
-          if (i == IY) g += pt[k - 1];
-        }
-        px[t] = g;
-        s2 += g * g;
-      } else if (t < nx + nuu) {
-        const int q = t - nx, k = q / NU, cc = q - NU * k;
-        R g = 0;
-        if (k < N - 1) {
-          const R* a = Bm + k * NX * NU + cc;
-          const R* f = ph + k * NX;
+      } else if (t < PX + PU) {
+        const int q = t - PX;
+        if (q < nuu) {
+          const int k = q / NU, cc = q - NU * k;
+          R g = 0;
+          if (k < N - 1) {
+            const R* a = Bm + k * NX * NU + cc;
+            const R* f = ph + k * NX;
 #pragma unroll
-          for (int r = 0; r < NX; ++r) g += a[r * NU] * f[r];
-        }
-        if (k > 0) {
-          const R* a = Bp + (k - 1) * NX * NU + cc;
-          const R* f = ph + (k - 1) * NX;
+            for (int r = 0; r < NX; ++r) g += a[r * NU] * f[r];
+          }
+          if (k > 0) {
+            const R* a = Bp + (k - 1) * NX * NU + cc;
+            const R* f = ph + (k - 1) * NX;
 #pragma unroll
-          for (int r = 0; r < NX; ++r) g += a[r * NU] * f[r];
+            for (int r = 0; r < NX; ++r) g += a[r * NU] * f[r];
+          }
+          pu[q] = g;
+          s2 += g * g;
         }
-        pu[q] = g;
-        s2 += g * g;
       } else {
-        const int q = t - nx - nuu;
-        const R f = ph[q];
-        pp[q] = f;
-        pn[q] = -f;
-        s2 += R(2) * f * f;
+        const int q = t - PX - PU;
+        if (q < nm) {
+          const R f = ph[q];
+          pp[q] = f;
+          pn[q] = -f;
+          s2 += R(2) * f * f;
+        }
       }
     }
     s2 = block_sum(s2, sm + L.red);
@@ -307,11 +332,18 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
 // phi, th), which hold the solution on return.  Readings: the mu^- step uses
 // (w_ep - phi); the B^+_{k-1} term of the u_k gradient multiplies the
 // extrapolated dual of the dynamics rows; the stop test compares iterates j+1
-// and j (the warm start being iterate 0).  Returns the iterations run.
+// and j (the warm start being iterate 0).
+// Work split, every task range padded to whole warps:
+//   primal phase: x_hat of nodes 2..N (15 (N-1) tasks), then u_hat (N nu
+//     tasks) and the fixed node 1 (15 tasks);
+//   dual phase: row i of interval k updates mu^+-, nu^+- (they read the same
+//     extrapolated dual entry) and then phi; then the CTCS rows theta_k.
+// Returns the iterations run.
 template <typename R, int NU>
 __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force) {
   const int N = L.N, T = blockDim.x, tid = threadIdx.x;
-  const int nx = N * NX, nuu = N * NU, nm = (N - 1) * NX;
+  const int nxk = (N - 1) * NX, nuk = N * NU + NX, nm = (N - 1) * NX;
+  const int PX = round32(nxk), PU = round32(nuk), PM = round32(nm);
   const R* __restrict__ Am = sm + L.Am;
   const R* __restrict__ Bm = sm + L.Bm;
   const R* __restrict__ Bp = sm + L.Bp;
@@ -335,13 +367,12 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
   R* vth = sm + L.vth;
   R* dx = sm + L.dx;
   R* du = sm + L.du;
-  R* dmu = sm + L.dmu;
-  for (int t = tid; t < nx + nuu + 2 * nm + (N - 1); t += T) {
-    if (t < nx) xt[t] = xh[t];
-    else if (t < nx + nuu) ut[t - nx] = uh[t - nx];
-    else if (t < nx + nuu + nm) { const int q = t - nx - nuu; nup[q] = mup[q]; num[q] = mum[q]; }
-    else if (t < nx + nuu + 2 * nm) { const int q = t - nx - nuu - nm; vph[q] = phi[q]; }
-    else { const int q = t - nx - nuu - 2 * nm; vth[q] = th[q]; }
+  for (int t = tid; t < N * NX + N * NU + 2 * nm + (N - 1); t += T) {
+    if (t < N * NX) xt[t] = xh[t];
+    else if (t < N * NX + N * NU) ut[t - N * NX] = uh[t - N * NX];
+    else if (t < N * NX + N * NU + nm) { const int q = t - N * NX - N * NU; nup[q] = mup[q]; num[q] = mum[q]; }
+    else if (t < N * NX + N * NU + 2 * nm) { const int q = t - N * NX - N * NU - nm; vph[q] = phi[q]; }
+    else { const int q = t - N * NX - N * NU - 2 * nm; vth[q] = th[q]; }
   }
   __syncthreads();
   const R wp = R(P.w_prox);
@@ -358,14 +389,12 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
     const bool chk = force <= 0 && jcheck > 0 && (j % jcheck) == 0;
     R zn = 0, zo = 0, zd = 0;
     // ---- projected gradient step (primal)
-    for (int t = tid; t < nx + nuu + nm; t += T) {
-      if (t < nx) {
-        const int k = t / NX, i = t - NX * k;
-        const R xv = xt[t];
-        R xn;
-        if (k == 0) {
-          xn = zi[i];
-        } else {
+    for (int t = tid; t < PX + PU; t += T) {
+      if (t < PX) {
+        if (t < nxk) {
+          const int k = t / NX + 1, i = t - NX * (k - 1);
+          const int o = k * NX + i;
+          const R xv = xt[o];
           R G = -vph[(k - 1) * NX + i];
           if (k < N - 1) {
             const R* a = Am + k * NX * NX + i;
@@ -376,92 +405,106 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           }
           if (i == IY) G += vth[k - 1];
           if (k == N - 1 && i == IM) G -= wcost;  // e_cost = -e_m (maximize m_N)
-          xn = c1 * xv - alpha * G;
+          R xn = c1 * xv - alpha * G;
           if (k == N - 1 && P.fix_f[i]) xn = zf[i];
+          dx[o] = R(2) * xn - xv;
+          xt[o] = xv + rho * (xn - xv);
+          if (chk) {
+            const R old = xh[o];
+            zn = rmax(zn, fabs(xn)); zo = rmax(zo, fabs(old)); zd = rmax(zd, fabs(xn - old));
+          }
+          xh[o] = xn;
         }
-        dx[t] = R(2) * xn - xv;
-        xt[t] = xv + rho * (xn - xv);
-        if (chk) {
-          const R o = xh[t];
-          zn = rmax(zn, fabs(xn)); zo = rmax(zo, fabs(o)); zd = rmax(zd, fabs(xn - o));
-        }
-        xh[t] = xn;
-      } else if (t < nx + nuu) {
-        const int q = t - nx, k = q / NU, cc = q - NU * k;
-        const R uv = ut[q];
-        R G = 0;
-        if (k < N - 1) {
-          const R* a = Bm + k * NX * NU + cc;
-          const R* f = vph + k * NX;
-#pragma unroll
-          for (int r = 0; r < NX; ++r) G += a[r * NU] * f[r];
-        }
-        if (k > 0) {
-          const R* a = Bp + (k - 1) * NX * NU + cc;
-          const R* f = vph + (k - 1) * NX;
-#pragma unroll
-          for (int r = 0; r < NX; ++r) G += a[r * NU] * f[r];
-        }
-        R un = c1 * uv - alpha * G;
-        if (cc == NU - 1) un = rmin(rmax(un, lo[k]), hi[k]);
-        du[q] = R(2) * un - uv;
-        ut[q] = uv + rho * (un - uv);
-        if (chk) {
-          const R o = uh[q];
-          zn = rmax(zn, fabs(un)); zo = rmax(zo, fabs(o)); zd = rmax(zd, fabs(un - o));
-        }
-        uh[q] = un;
       } else {
-        const int q = t - nx - nuu;
-        const R f = vph[q], a = nup[q], b = num[q];
-        const R mp = rmax(R(0), a - alpha * (wep + f));
-        const R mm = rmax(R(0), b - alpha * (wep - f));
-        dmu[q] = (R(2) * mp - a) - (R(2) * mm - b);
-        nup[q] = a + rho * (mp - a);
-        num[q] = b + rho * (mm - b);
-        if (chk) {
-          const R op = mup[q], om = mum[q];
-          zn = rmax(zn, rmax(mp, mm)); zo = rmax(zo, rmax(op, om));
-          zd = rmax(zd, rmax(fabs(mp - op), fabs(mm - om)));
+        const int q = t - PX;
+        if (q < N * NU) {
+          const int k = q / NU, cc = q - NU * k;
+          const R uv = ut[q];
+          R G = 0;
+          if (k < N - 1) {
+            const R* a = Bm + k * NX * NU + cc;
+            const R* f = vph + k * NX;
+#pragma unroll
+            for (int r = 0; r < NX; ++r) G += a[r * NU] * f[r];
+          }
+          if (k > 0) {
+            const R* a = Bp + (k - 1) * NX * NU + cc;
+            const R* f = vph + (k - 1) * NX;
+#pragma unroll
+            for (int r = 0; r < NX; ++r) G += a[r * NU] * f[r];
+          }
+          R un = c1 * uv - alpha * G;
+          if (cc == NU - 1) un = rmin(rmax(un, lo[k]), hi[k]);
+          du[q] = R(2) * un - uv;
+          ut[q] = uv + rho * (un - uv);
+          if (chk) {
+            const R old = uh[q];
+            zn = rmax(zn, fabs(un)); zo = rmax(zo, fabs(old)); zd = rmax(zd, fabs(un - old));
+          }
+          uh[q] = un;
+        } else if (q < nuk) {
+          // node 1: every component fixed by E_i
+          const int i = q - N * NU;
+          const R xv = xt[i], xn = zi[i];
+          dx[i] = R(2) * xn - xv;
+          xt[i] = xv + rho * (xn - xv);
+          if (chk) {
+            const R old = xh[i];
+            zn = rmax(zn, fabs(xn)); zo = rmax(zo, fabs(old)); zd = rmax(zd, fabs(xn - old));
+          }
+          xh[i] = xn;
         }
-        mup[q] = mp;
-        mum[q] = mm;
       }
     }
     __syncthreads();
-    // ---- proportional-integral feedback (dual)
+    // ---- virtual controls and proportional-integral feedback (dual)
     R rn = 0, ro = 0, rd = 0;
-    for (int t = tid; t < nm + (N - 1); t += T) {
-      if (t < nm) {
-        const int k = t / NX, i = t - NX * k;
-        const R* a = Am + (k * NX + i) * NX;
-        const R* d = dx + k * NX;
-        R r = wv[t] + dmu[t] - dx[(k + 1) * NX + i];
+    for (int t = tid; t < PM + 32; t += T) {
+      if (t < PM) {
+        if (t < nm) {
+          const int k = t / NX, i = t - NX * k;
+          const R f = vph[t], a = nup[t], b = num[t];
+          const R mp = max0(a - alpha * (wep + f));
+          const R mm = max0(b - alpha * (wep - f));
+          nup[t] = a + rho * (mp - a);
+          num[t] = b + rho * (mm - b);
+          if (chk) {
+            const R op = mup[t], om = mum[t];
+            zn = rmax(zn, rmax(mp, mm)); zo = rmax(zo, rmax(op, om));
+            zd = rmax(zd, rmax(fabs(mp - op), fabs(mm - om)));
+          }
+          mup[t] = mp;
+          mum[t] = mm;
+          const R* a_ = Am + (k * NX + i) * NX;
+          const R* d = dx + k * NX;
+          R r = wv[t] + ((R(2) * mp - a) - (R(2) * mm - b)) - dx[(k + 1) * NX + i];
 #pragma unroll
-        for (int cc = 0; cc < NX; ++cc) r += a[cc] * d[cc];
-        const R* bm = Bm + (k * NX + i) * NU;
-        const R* bp = Bp + (k * NX + i) * NU;
+          for (int cc = 0; cc < NX; ++cc) r += a_[cc] * d[cc];
+          const R* bm = Bm + (k * NX + i) * NU;
+          const R* bp = Bp + (k * NX + i) * NU;
 #pragma unroll
-        for (int cc = 0; cc < NU; ++cc) r += bm[cc] * du[k * NU + cc] + bp[cc] * du[(k + 1) * NU + cc];
-        const R v = vph[t];
-        const R pn = v + beta * r;
-        vph[t] = v + rho * (pn - v);
-        if (chk) {
-          const R o = phi[t];
-          rn = rmax(rn, fabs(pn)); ro = rmax(ro, fabs(o)); rd = rmax(rd, fabs(pn - o));
+          for (int cc = 0; cc < NU; ++cc) r += bm[cc] * du[k * NU + cc] + bp[cc] * du[(k + 1) * NU + cc];
+          const R pn = f + beta * r;
+          vph[t] = f + rho * (pn - f);
+          if (chk) {
+            const R old = phi[t];
+            rn = rmax(rn, fabs(pn)); ro = rmax(ro, fabs(old)); rd = rmax(rd, fabs(pn - old));
+          }
+          phi[t] = pn;
         }
-        phi[t] = pn;
       } else {
-        const int k = t - nm;
-        const R hy = dx[(k + 1) * NX + IY] - dx[k * NX + IY] - ep[k];
-        const R v = vth[k];
-        const R tn = rmax(R(0), v + beta * hy);
-        vth[k] = v + rho * (tn - v);
-        if (chk) {
-          const R o = th[k];
-          rn = rmax(rn, tn); ro = rmax(ro, fabs(o)); rd = rmax(rd, fabs(tn - o));
+        const int k = t - PM;
+        if (k < N - 1) {
+          const R hy = dx[(k + 1) * NX + IY] - dx[k * NX + IY] - ep[k];
+          const R v = vth[k];
+          const R tn = max0(v + beta * hy);
+          vth[k] = v + rho * (tn - v);
+          if (chk) {
+            const R old = th[k];
+            rn = rmax(rn, tn); ro = rmax(ro, fabs(old)); rd = rmax(rd, fabs(tn - old));
+          }
+          th[k] = tn;
         }
-        th[k] = tn;
       }
     }
     if (chk) {
