@@ -145,6 +145,29 @@ int pdg_mc_launch_info(pdg_handle* h, int* threads, int* ctas_per_sm, int* smem_
  * automatic).  Used by the autotuner. */
 int pdg_mc_set_threads(pdg_handle* h, int threads);
 
+/* Solve without allocating: for callers that cannot call cudaMalloc while
+ * they run, e.g. code inside a region that a memory pool or allocator owns,
+ * or a host that must not grow its device footprint after start-up.  The
+ * paper has no counterpart.  Same arguments, results and status codes as
+ * pdg_mc_solve_batch in plain form (mode 0), except: no trace; every SCP
+ * iteration up to scp_jmax is launched (finished instances return at once)
+ * and the call never synchronizes the stream.  The per-instance workspace
+ * lives in a fixed 32 MiB device array that the library defines, so every
+ * GPU that loads the library holds those 32 MiB until the process exits.
+ *   - Batches that need more than the 32 MiB (about 650 instances at
+ *     n_max = 15 in FP64, twice that in FP32) are rejected with PDG_EINVAL
+ *     and a message that states the limit; nothing is launched.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture on that device.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (other streams, other threads) race and corrupt each other.  Serialize
+ *     them, e.g. on one stream.
+ * No cudaMalloc, cudaFree or other allocating call is made. */
+int pdg_mc_solve_batch_noalloc(pdg_handle* h, int B, const double* x0, const int* n_nodes,
+                               double* X, double* U, double* tf, double* fuel, int* status,
+                               int* scp_iters, long long* pipg_iters, void* cuda_stream);
+
 /* Roofline denominator probe (no counterpart in the paper): runs an FMA-chain
  * kernel on all SMs of the current device in FP64 (precision 0) or FP32 (1)
  * and writes the best of three timed launches, in TFLOP/s, to *tflops.

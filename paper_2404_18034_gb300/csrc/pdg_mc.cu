@@ -16,6 +16,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 
 #include "../../include/pdg_mc.h"
@@ -376,6 +377,13 @@ __global__ void k_fma_probe(int iters, R seed, R* out) {
 }  // namespace
 
 // ===========================================================================
+// scratch for pdg_mc_solve_batch_noalloc: a fixed device array, so that the
+// entry point never allocates (see include/pdg_mc.h)
+// ===========================================================================
+static constexpr size_t kNoAllocBytes = size_t(32) << 20;  // 32 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// ===========================================================================
 // host side
 // ===========================================================================
 struct pdg_handle {
@@ -674,6 +682,78 @@ static int run_step(pdg_handle* h, int B, const double* x0, const int* Ns, doubl
   return 0;
 }
 
+// Device address of g_noalloc_scratch for the current device, looked up once
+// per device (the host-side name of the array is not a device address).
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[64];
+
+static int noalloc_scratch(pdg_handle* h, void** out) {
+  int dev = 0;
+  PDG_CUDA(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(h, PDG_EINVAL, "device index out of range for the static scratch table");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(h, PDG_ECUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return 0;
+}
+
+template <typename R, int NU>
+static int run_noalloc(pdg_handle* h, int B, const double* x0, const int* Ns, double* X, double* U, double* tf,
+                       double* fuel, int* status, int* scp_iters, long long* pipg_iters, cudaStream_t s) {
+  const int T = pick_threads(h);
+  const Lay L = make_lay(h->n_max, NU, T);
+  const size_t smem = (size_t)L.total * sizeof(R);
+  if (L.ipw < 1) return fail(h, PDG_EINVAL, "threads per CTA too small for one discretization interval");
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t istride = (size_t)L.img;
+  const size_t per = istride * sizeof(R) + sizeof(long long) + 4 * sizeof(int);
+  const size_t fixed = al(sizeof(int) * 2) + 3 * 256;
+  const size_t need = al(sizeof(int) * (4 * (size_t)B + 2)) + al(sizeof(long long) * (size_t)B) + al(istride * sizeof(R) * B);
+  if (need > kNoAllocBytes) {
+    const size_t bmax = (kNoAllocBytes - fixed) / per;
+    char msg[200];
+    snprintf(msg, sizeof msg, "batch of %d needs %zu bytes of scratch; the static scratch holds %zu bytes (at most about %zu instances for this n_max and precision)",
+             B, need, kNoAllocBytes, bmax);
+    return fail(h, PDG_EINVAL, msg);
+  }
+  void* base = nullptr;
+  if (int rc = noalloc_scratch(h, &base)) return rc;
+  if (int rc = Kern<R, NU>::prepare(h, T, smem)) return rc;
+  char* c = (char*)base;
+  PlainWs W;
+  W.st = (int*)c;
+  W.sit = W.st + B;
+  W.pow_it = W.st + 2 * (size_t)B;
+  W.pipg_it = W.st + 3 * (size_t)B;
+  W.done = W.st + 4 * (size_t)B;
+  c += al(sizeof(int) * (4 * (size_t)B + 2));
+  W.lit = (long long*)c;
+  c += al(sizeof(long long) * (size_t)B);
+  W.img = c;
+  W.istride = (int)istride;
+  // the array keeps the previous call's contents: clear the counter (every
+  // per-instance field is written by k_plain_init before it is read)
+  PDG_CUDA(h, cudaMemsetAsync(W.done, 0, sizeof(int), s));
+  k_plain_init<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, W, X, U, tf, fuel, status, scp_iters, pipg_iters);
+  for (int j = 0; j < h->p.scp_jmax; ++j) {
+    k_plain_disc<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W);
+    k_plain_power<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
+    k_plain_pipg<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
+    k_plain_update<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, 0, X, U, tf, fuel, status, scp_iters,
+                                              pipg_iters, nullptr, nullptr);
+  }
+  PDG_CUDA(h, cudaGetLastError());
+  h->last_threads = T;
+  h->last_smem = (int)smem;
+  return 0;
+}
+
 #define PDG_DISPATCH(h, fn, ...)                                         \
   ((h)->p.precision == 0                                                 \
        ? ((h)->p.nu == 4 ? fn<double, 4>(__VA_ARGS__) : fn<double, 7>(__VA_ARGS__)) \
@@ -822,6 +902,19 @@ int pdg_mc_set_threads(pdg_handle* h, int threads) {
   if (threads < 0 || threads > 512 || (threads % 32) != 0) return fail(h, PDG_EINVAL, "threads must be 0 or a multiple of 32 up to 512");
   h->threads_override = threads;
   return PDG_OK;
+}
+
+int pdg_mc_solve_batch_noalloc(pdg_handle* h, int B, const double* x0, const int* n_nodes, double* X, double* U,
+                               double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
+                               void* cuda_stream) {
+  if (!h) return PDG_EINVAL;
+  h->err.clear();
+  if (B < 0) return fail(h, PDG_EINVAL, "B must be >= 0");
+  if (B == 0) return PDG_OK;
+  if (!x0 || !X || !U || !tf || !fuel || !status || !scp_iters || !pipg_iters) return fail(h, PDG_EINVAL, "NULL buffer");
+  PDG_CUDA(h, cudaSetDevice(h->device));
+  return PDG_DISPATCH(h, run_noalloc, h, B, x0, n_nodes, X, U, tf, fuel, status, scp_iters, pipg_iters,
+                      (cudaStream_t)cuda_stream);
 }
 
 int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream) {

@@ -22,7 +22,7 @@ PDG_CONVERGED, PDG_MAX_SCP, PDG_NONFINITE, PDG_BUDGET, PDG_BAD_INPUT = 0, 1, 2, 
 ERRORS = {-1: "PDG_EINVAL", -2: "PDG_ENOMEM", -3: "PDG_ECUDA"}
 EXPORTS = ("pdg_mc_init", "pdg_mc_destroy", "pdg_mc_last_error", "pdg_mc_solve_batch",
            "pdg_mc_solve_batch_host", "pdg_mc_subproblem", "pdg_mc_scp_step", "pdg_mc_launch_info",
-           "pdg_mc_set_threads", "pdg_mc_probe_fma")
+           "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc")
 
 
 class PdgParams(C.Structure):
@@ -71,8 +71,9 @@ def load_library(path: str = LIB_PATH):
     L.pdg_mc_launch_info.argtypes = [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.pdg_mc_set_threads.argtypes = [_VP, C.c_int]
     L.pdg_mc_probe_fma.argtypes = [C.c_int, C.POINTER(C.c_double), _VP]
+    L.pdg_mc_solve_batch_noalloc.argtypes = [_VP, C.c_int, _VP, _VP] + [_VP] * 7 + [_VP]
     for name in ("pdg_mc_init", "pdg_mc_solve_batch", "pdg_mc_solve_batch_host", "pdg_mc_subproblem",
-                 "pdg_mc_scp_step", "pdg_mc_launch_info", "pdg_mc_set_threads", "pdg_mc_probe_fma"):
+                 "pdg_mc_scp_step", "pdg_mc_launch_info", "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -179,6 +180,18 @@ class Solver:
                                          _ptr(out["scp_iters"]), _ptr(out["pipg_iters"]), _ptr(tr),
                                          self._stream(stream))
         self._check(rc, "pdg_mc_solve_batch")
+        return out
+
+    def solve_noalloc(self, x0, n_nodes=None, out=None, stream=None):
+        """pdg_mc_solve_batch_noalloc: the plain-form solve with its workspace in
+        the library's fixed device scratch array (no allocation in the call)."""
+        B = int(x0.shape[0])
+        out = out or self.alloc_outputs(B, x0.device)
+        rc = self.lib.pdg_mc_solve_batch_noalloc(self.h, B, _ptr(x0), _ptr(n_nodes), _ptr(out["X"]), _ptr(out["U"]),
+                                                 _ptr(out["tf"]), _ptr(out["fuel"]), _ptr(out["status"]),
+                                                 _ptr(out["scp_iters"]), _ptr(out["pipg_iters"]),
+                                                 self._stream(stream))
+        self._check(rc, "pdg_mc_solve_batch_noalloc")
         return out
 
     def solve_host(self, x0: np.ndarray, n_nodes: Optional[np.ndarray] = None, mode: int = 1, out=None,
