@@ -87,7 +87,7 @@ __device__ void write_outputs(const Lay& L, const R* sm, int b, int Nmax, int st
 // persistent form
 // ---------------------------------------------------------------------------
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
              double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
              int* trace, int* queue) {
@@ -165,7 +165,7 @@ struct PlainWs {
 };
 
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 k_plain_init(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns, PlainWs W,
              double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -194,7 +194,7 @@ k_plain_init(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
 }
 
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 k_plain_disc(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -213,7 +213,7 @@ k_plain_disc(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plain
 }
 
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 k_plain_power(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, const int* force) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -231,7 +231,7 @@ k_plain_power(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plai
 }
 
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 k_plain_pipg(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, const int* force) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -250,7 +250,7 @@ k_plain_pipg(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plain
 
 // step_only: the one-iteration API (no status, no outputs).
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 k_plain_update(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, int step_only,
                double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
                int* trace, double* step_out) {
@@ -298,7 +298,7 @@ k_plain_update(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Pla
 // API helpers: subproblem data and one-iteration packing
 // ---------------------------------------------------------------------------
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 k_subproblem(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
              const double* __restrict__ X, const double* __restrict__ U, double* Am, double* Bm, double* Bp, double* w) {
   extern __shared__ __align__(16) unsigned char smraw[];

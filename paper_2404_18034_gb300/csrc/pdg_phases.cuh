@@ -64,7 +64,7 @@ __device__ void phase_init_guess(const DParams& P, const Lay& L, R* sm) {
 // interval) in registers.  Intervals are processed in waves of L.ipw.
 // Returns max_k |hat w_k|_inf (the scaled defect) on every thread.
 template <typename R, int NU>
-__device__ R phase_discretize(const DParams& P, const Lay& L, R* sm) {
+__device__ __noinline__ R phase_discretize(const DParams& P, const Lay& L, R* sm) {
   constexpr int NCOL = NX + 2 * NU;
   const int N = L.N;
   const R* Xb = sm + L.Xb;
@@ -380,6 +380,7 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
   const R beta = R(P.omega) * alpha;
   const R c1 = R(1) - alpha * wp;
   const R rho = R(P.rho);
+  const R rb = rho * beta;
   const R wcost = R(P.w_cost), wep = R(P.w_ep);
   const R eabs = R(P.eps_abs), erel = R(P.eps_rel);
   const int jmax = force > 0 ? force : P.pipg_jmax;
@@ -399,8 +400,13 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           if (k < N - 1) {
             const R* a = Am + k * NX * NX + i;
             const R* f = vph + k * NX;
+            R G2 = 0;
 #pragma unroll
-            for (int r = 0; r < NX; ++r) G += a[r * NX] * f[r];
+            for (int r = 0; r < NX; r += 2) {
+              G += a[r * NX] * f[r];
+              if (r + 1 < NX) G2 += a[(r + 1) * NX] * f[r + 1];
+            }
+            G += G2;
             if (i == IY) G -= vth[k];
           }
           if (i == IY) G += vth[k - 1];
@@ -420,7 +426,7 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
         if (q < N * NU) {
           const int k = q / NU, cc = q - NU * k;
           const R uv = ut[q];
-          R G = 0;
+          R G = 0, G2 = 0;
           if (k < N - 1) {
             const R* a = Bm + k * NX * NU + cc;
             const R* f = vph + k * NX;
@@ -431,8 +437,9 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
             const R* a = Bp + (k - 1) * NX * NU + cc;
             const R* f = vph + (k - 1) * NX;
 #pragma unroll
-            for (int r = 0; r < NX; ++r) G += a[r * NU] * f[r];
+            for (int r = 0; r < NX; ++r) G2 += a[r * NU] * f[r];
           }
+          G += G2;
           R un = c1 * uv - alpha * G;
           if (cc == NU - 1) un = rmin(rmax(un, lo[k]), hi[k]);
           du[q] = R(2) * un - uv;
@@ -478,14 +485,19 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           const R* a_ = Am + (k * NX + i) * NX;
           const R* d = dx + k * NX;
           R r = wv[t] + ((R(2) * mp - a) - (R(2) * mm - b)) - dx[(k + 1) * NX + i];
+          R r2 = 0;
 #pragma unroll
-          for (int cc = 0; cc < NX; ++cc) r += a_[cc] * d[cc];
+          for (int cc = 0; cc < NX; cc += 2) {
+            r += a_[cc] * d[cc];
+            if (cc + 1 < NX) r2 += a_[cc + 1] * d[cc + 1];
+          }
           const R* bm = Bm + (k * NX + i) * NU;
           const R* bp = Bp + (k * NX + i) * NU;
 #pragma unroll
-          for (int cc = 0; cc < NU; ++cc) r += bm[cc] * du[k * NU + cc] + bp[cc] * du[(k + 1) * NU + cc];
+          for (int cc = 0; cc < NU; ++cc) { r += bm[cc] * du[k * NU + cc]; r2 += bp[cc] * du[(k + 1) * NU + cc]; }
+          r += r2;
           const R pn = f + beta * r;
-          vph[t] = f + rho * (pn - f);
+          vph[t] = f + rb * r;  // = f + rho (pn - f)
           if (chk) {
             const R old = phi[t];
             rn = rmax(rn, fabs(pn)); ro = rmax(ro, fabs(old)); rd = rmax(rd, fabs(pn - old));

@@ -123,7 +123,8 @@ def probe_fma(precision: int = 0, stream=None) -> float:
 class Solver:
     """Handle on the batched solver (pdg_mc_init / pdg_mc_destroy)."""
 
-    def __init__(self, params: Dict, n_max: int, precision: int = 0, budget_seconds: float = 0.0):
+    def __init__(self, params: Dict, n_max: int, precision: int = 0, budget_seconds: float = 0.0,
+                 tune_cache: Optional[str] = None, mode: int = 1):
         self.lib = load_library()
         self.params = params
         self.nu = int(params["nu"])
@@ -135,6 +136,15 @@ class Solver:
         if rc != 0:
             raise RuntimeError(f"pdg_mc_init: {ERRORS.get(rc, rc)}: {self.lib.pdg_mc_last_error(None).decode()}")
         self.h = h
+        self.tuned_threads = None
+        if tune_cache:
+            import torch
+
+            from .autotune import lookup
+            t = lookup(torch.cuda.get_device_name(), self.n_max, self.nu, self.precision, mode, tune_cache)
+            if t:
+                self.set_threads(t)
+                self.tuned_threads = t
 
     def close(self):
         if getattr(self, "h", None):
