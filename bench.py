@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=16384)
     ap.add_argument("--nodes", type=int, default=15)
     ap.add_argument("--dispersion", default="bj")
+    ap.add_argument("--uneven", action="store_true", help="N per instance uniform in {10, 15, 20, 30}")
+    ap.add_argument("--grad", action="store_true", help="time gradients (pdg_mc_grad_batch) instead of solves")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -53,7 +55,8 @@ def parse():
 
 
 def workload_name(a):
-    return f"pdg6dof_{a.dispersion}_B{a.batch}_N{a.nodes}_{a.precision}_{a.mode}"
+    n = "Nuneven10-30" if a.uneven else f"N{a.nodes}"
+    return f"pdg6dof_{a.dispersion}_B{a.batch}_{n}_{a.precision}_{a.mode}"
 
 
 class ClockSampler:
@@ -166,6 +169,48 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def run_grad(a):
+    """Gradient workload: B dispersed instances, d(fuel, touchdown)/d(x0, m_wet)."""
+    import torch
+
+    from paper_2404_18034_gb300 import build, inputs
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p = inputs.load_params()
+    x0 = torch.from_numpy(inputs.dispersion(p, a.batch, inputs.config_seed(3), a.dispersion)).to(dev)
+    S = Solver(p, a.nodes, 0)
+    gf = torch.ones(a.batch, dtype=torch.float64, device=dev)
+    gt = torch.ones(a.batch, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(a.warmup):
+        o = S.grad(x0, None, gf, gt)
+    torch.cuda.synchronize(dev)
+    ms, ok = [], 0
+    with ClockSampler(0) as clk:
+        for _ in range(a.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o = S.grad(x0, None, gf, gt)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+            ok += int((o["status"] <= 1).sum().item())
+    line = {"metric": "gradients d(fuel, touchdown)/d(x0, m_wet) per second on 1 GB300, batch 4096, N=15",
+            "value": ok / (sum(ms) * 1e-3), "unit": "grads/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"pdg6dof_grad_{a.dispersion}_B{a.batch}_N{a.nodes}_fp64", "batch": a.batch,
+                       "nodes": a.nodes, "l2": "256 MiB buffer written between timed steps",
+                       "includes": "the forward solve and the adjoint of its last SCP iteration"},
+            "clocks": clk.summary(), "gpu_launches": 2 * a.steps}
+    print(json.dumps(line), flush=True)
+    S.close()
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -189,6 +234,10 @@ def run_ours(a):
     seed = inputs.config_seed(2) + 1000 * rank
     x0h = inputs.dispersion(p, a.batch, seed, a.dispersion)
     x0 = torch.from_numpy(x0h).to(dev)
+    Ns_h = inputs.node_counts(a.batch, seed) if a.uneven else None
+    Ns = torch.from_numpy(Ns_h).to(dev) if a.uneven else None
+    if a.uneven:
+        a.nodes = int(Ns_h.max())
     mode = 1 if a.mode == "persistent" else 0
     from paper_2404_18034_gb300.autotune import DEFAULT_CACHE
     S = Solver(p, a.nodes, prec, tune_cache=DEFAULT_CACHE, mode=mode)
@@ -197,7 +246,7 @@ def run_ours(a):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
     def step(trace=False):
-        return S.solve(x0, None, mode=mode, out=out, trace=trace, stream=stream)
+        return S.solve(x0, Ns, mode=mode, out=out, trace=trace, stream=stream)
 
     for _ in range(a.warmup):
         step()
@@ -237,7 +286,8 @@ def run_ours(a):
     value = float(stats[1]) / (total_ms_max * 1e-3)
 
     # roofline of the dominant kernel (the persistent solve kernel is the whole step)
-    fl = flops.solve_flops(np.full(a.batch, a.nodes), p["nu"], p["rk4_substeps"], scp, pow_it, pipg)
+    fl = flops.solve_flops(Ns_h if a.uneven else np.full(a.batch, a.nodes), p["nu"], p["rk4_substeps"], scp, pow_it,
+                           pipg)
     launch_s = float(np.mean(ms)) * 1e-3
     achieved = fl / launch_s / 1e12
     clocks = clk.summary()
@@ -254,13 +304,13 @@ def run_ours(a):
         x0_pinned = pin.numpy()
         outs = {k: torch.empty(tuple(v.shape), dtype=v.dtype).pin_memory().numpy() for k, v in out.items()
                 if k != "trace"}
-        S.solve_host(x0_pinned, None, mode=mode, out=outs, stream=stream)
+        S.solve_host(x0_pinned, Ns_h, mode=mode, out=outs, stream=stream)
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         e2e_conv = 0
         for _ in range(a.steps):
-            r = S.solve_host(x0_pinned, None, mode=mode, out=outs, stream=stream)
+            r = S.solve_host(x0_pinned, Ns_h, mode=mode, out=outs, stream=stream)
             e2e_conv += int(np.sum(r["status"] == 0))
         e2e_s = time.perf_counter() - t0
         es = torch.tensor([e2e_s, e2e_conv], dtype=torch.float64, device=dev)
@@ -270,7 +320,7 @@ def run_ours(a):
             c = es[1:].clone()
             dist.all_reduce(c, op=dist.ReduceOp.SUM)
             es = torch.cat([t_max, c])
-        h2d = x0h.nbytes
+        h2d = x0h.nbytes + (Ns_h.nbytes if a.uneven else 0)
         d2h = sum(v.nbytes for v in outs.values())
         e2e = {"value": float(es[1]) / float(es[0]), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
@@ -286,7 +336,7 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": total_ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
             "config": {"workload": workload_name(a), "batch_per_gpu": a.batch, "global_batch": a.batch * world,
-                       "nodes": a.nodes, "nu": p["nu"], "precision": a.precision, "mode": a.mode,
+                       "nodes": "uniform in {10,15,20,30}" if a.uneven else a.nodes, "nu": p["nu"], "precision": a.precision, "mode": a.mode,
                        "dispersion": a.dispersion, "parallelism": f"dp{world}",
                        "l2": "256 MiB buffer written between timed steps",
                        "threads_per_cta": info["threads"], "ctas_per_sm": info["ctas_per_sm"],
@@ -315,6 +365,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.grad:
+        run_grad(a)
     else:
         run_ours(a)
 

@@ -136,6 +136,28 @@ int pdg_mc_scp_step(pdg_handle* h, int B, const double* x0, const int* n_nodes,
                     double* phi, double* th, const int* force,
                     double* sigma, double* defect, double* step, int* iters, void* cuda_stream);
 
+/* Gradients of the converged outputs with respect to the initial state and
+ * wet mass (FP64 handles only).  Solves the batch (persistent form), then
+ * differentiates the solve's last SCP iteration as a function of x0 -- the
+ * reference's first node moving with x0, the rest of that iteration's
+ * reference, its PIPG warm start, step size and iteration count held --
+ * through the RK4 discretization of the first interval (Sec. 2.3.1, forward
+ * mode), the prescaling (Sec. 2.3.2) and the final PIPG_custom loop (reverse
+ * mode, recomputed from checkpoints every 50 iterations, projections masked as
+ * in the forward pass).  The paper has no gradient; this definition is the
+ * solver's own.  Device buffers:
+ *   dL_dfuel, dL_dtouch [B]  upstream cotangents (NULL = zero)
+ *   grad_x0 [B][14]          d L / d (m_wet, r, v, q, w), with
+ *                            L = dL_dfuel fuel + dL_dtouch touchdown
+ *   fuel [B], touch [B]      outputs (NULL = not written): fuel = m_1 - m_N and
+ *                            touchdown = 0.5 sum_{E_f} ((x_prop,N - z_f)/P_x)^2,
+ *                            x_prop,N the RK4 propagation of the last interval
+ *   status [B]               solve status (NULL = not written); instances that
+ *                            end non-finite or with bad input get zero gradient */
+int pdg_mc_grad_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes,
+                      const double* dL_dfuel, const double* dL_dtouch, double* grad_x0,
+                      double* fuel, double* touch, int* status, void* cuda_stream);
+
 /* Shape of the last launch configuration chosen for (n_max, nu, precision):
  * threads per CTA, CTAs per SM and dynamic shared memory per CTA (bytes).
  * Synchronous; no device work. */

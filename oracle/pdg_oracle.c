@@ -927,7 +927,7 @@ void orc_init_guess(const orc_params* p, int N, const double* x0, double* X, dou
 }
 
 int orc_scp_iterate(const orc_params* p, int N, const double* x0, double* X, double* U,
-                    orc_pd* ws, int force_pow, int force_pipg,
+                    orc_pd* ws, int force_pow, int force_pipg, double force_sigma,
                     double* sigma, int* pow_it, int* pipg_it, double* defect, double* step) {
   const int nu = p->nu;
   double* A = malloc(sizeof(double) * (N - 1) * NX * NX);
@@ -939,7 +939,7 @@ int orc_scp_iterate(const orc_params* p, int N, const double* x0, double* X, dou
   orc_discretize(p, N, X, U, A, Bm, Bp, xp);
   orc_scale(p, N, x0, X, U, A, Bm, Bp, xp, &qp);
   int pit = 0;
-  double sg = orc_power(p, &qp, ws, force_pow, &pit);
+  double sg = force_sigma > 0 ? force_sigma : orc_power(p, &qp, ws, force_pow, &pit);
   int jit = orc_pipgc(p, &qp, sg, ws, force_pipg);
   double dfc = infn((N - 1) * NX, qp.w);
   double stp = maxd(infn(N * NX, ws->xh), infn(N * nu, ws->uh));
@@ -955,6 +955,22 @@ int orc_scp_iterate(const orc_params* p, int N, const double* x0, double* X, dou
   orc_qp_free(&qp);
   free(A); free(Bm); free(Bp); free(xp);
   return 0;
+}
+
+/* Touchdown error of a trajectory: the last interval propagated by the same
+ * RK4 (Eq. disc-dyn) from (x_{N-1}, u_{N-1}, u_N), compared with z_f on the
+ * components E_f fixes, scaled by P_x: 0.5 sum ((x_prop - z_f) / P_x)^2. */
+double orc_touchdown(const orc_params* p, int N, const double* X, const double* U) {
+  const int nu = p->nu;
+  double xp[NX];
+  flow_dtau(p, X + (N - 2) * NX, U + (N - 2) * nu, U + (N - 1) * nu, 1.0 / (N - 1), p->rk4_substeps, xp);
+  double e = 0;
+  for (int i = 0; i < NX; i++)
+    if (p->fix_f[i]) {
+      double d = (xp[i] - p->z_f[i]) / p->P_x[i];
+      e += 0.5 * d * d;
+    }
+  return e;
 }
 
 static int all_finite(int n, const double* a) {
@@ -981,7 +997,7 @@ int orc_solve(const orc_params* p, int N, const double* x0, double* X, double* U
     if (replay) { fp = trace[(j - 1) * 2 + 0]; fj = trace[(j - 1) * 2 + 1]; }
     int pit, jit;
     double sg, dfc, stp;
-    orc_scp_iterate(p, N, x0, X, U, &ws, fp, fj, &sg, &pit, &jit, &dfc, &stp);
+    orc_scp_iterate(p, N, x0, X, U, &ws, fp, fj, 0.0, &sg, &pit, &jit, &dfc, &stp);
     if (trace && !replay) { trace[(j - 1) * 2 + 0] = pit; trace[(j - 1) * 2 + 1] = jit; }
     res->pipg_iters += jit;
     res->pow_iters += pit;

@@ -135,10 +135,15 @@ typedef struct orc_result {
 
 /* One SCP iteration about (X, U): discretize, scale, power iteration, PIPG.
  * ws: warm start in / subproblem solution out.  Outputs the subproblem data
- * measures and counts.  force_pipg / force_pow > 0 replay given counts. */
+ * measures and counts.  force_pipg / force_pow > 0 replay given counts;
+ * force_sigma > 0 replaces the power iteration's estimate. */
 int orc_scp_iterate(const orc_params* p, int N, const double* x0, double* X, double* U,
-                    orc_pd* ws, int force_pow, int force_pipg,
+                    orc_pd* ws, int force_pow, int force_pipg, double force_sigma,
                     double* sigma, int* pow_it, int* pipg_it, double* defect, double* step);
+
+/* Touchdown error 0.5 sum_{E_f} ((x_prop,N - z_f) / P_x)^2 of a trajectory,
+ * x_prop,N the RK4 propagation of the last interval. */
+double orc_touchdown(const orc_params* p, int N, const double* X, const double* U);
 
 /* Full solve.  trace (may be NULL) is [scp_jmax][2] = (power iters, PIPG iters)
  * per SCP iteration, written on output; when replay != 0 it is read instead and

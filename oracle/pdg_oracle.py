@@ -113,8 +113,10 @@ def lib():
             L.orc_sym_eig_max.argtypes = [C.c_int, _DP]
             L.orc_sym_eig_max.restype = C.c_double
             L.orc_init_guess.argtypes = [P, C.c_int, _DP, _DP, _DP]
-            L.orc_scp_iterate.argtypes = [P, C.c_int, _DP, _DP, _DP, C.POINTER(PD), C.c_int, C.c_int,
+            L.orc_scp_iterate.argtypes = [P, C.c_int, _DP, _DP, _DP, C.POINTER(PD), C.c_int, C.c_int, C.c_double,
                                           _DP, _IP, _IP, _DP, _DP]
+            L.orc_touchdown.argtypes = [P, C.c_int, _DP, _DP]
+            L.orc_touchdown.restype = C.c_double
             L.orc_solve.argtypes = [P, C.c_int, _DP, _DP, _DP, C.POINTER(Result), _IP, C.c_int, C.c_int]
             L.orc_solve_batch.argtypes = [P, C.c_int, C.c_int, _IP, _DP, _DP, _DP, _DP, _DP, _IP, _IP,
                                           C.POINTER(C.c_longlong), C.c_int]
@@ -348,14 +350,44 @@ def init_guess(p, N, x0):
     return X, U
 
 
-def scp_iterate(p, x0, X, U, ws: PDState, force_pow=0, force_pipg=0):
+def scp_iterate(p, x0, X, U, ws: PDState, force_pow=0, force_pipg=0, force_sigma=0.0):
     """One SCP iteration in place on (X, U, ws)."""
     sig = C.c_double(); pit = C.c_int(); jit = C.c_int(); dfc = C.c_double(); stp = C.c_double()
     ss = ws.cstruct()
     lib().orc_scp_iterate(C.byref(make_params(p)), X.shape[0], _d(np.ascontiguousarray(x0, np.float64)),
-                          _d(X), _d(U), C.byref(ss), int(force_pow), int(force_pipg),
+                          _d(X), _d(U), C.byref(ss), int(force_pow), int(force_pipg), float(force_sigma),
                           C.byref(sig), C.byref(pit), C.byref(jit), C.byref(dfc), C.byref(stp))
     return dict(sigma=sig.value, pow_iters=pit.value, pipg_iters=jit.value, defect=dfc.value, step=stp.value)
+
+
+def touchdown(p, X, U):
+    """Touchdown error of a trajectory (see orc_touchdown)."""
+    X = np.ascontiguousarray(X, np.float64); U = np.ascontiguousarray(U, np.float64)
+    return lib().orc_touchdown(C.byref(make_params(p)), X.shape[0], _d(X), _d(U))
+
+
+def final_iteration_state(p, N, x0, trace, scp_iters):
+    """Replay a solve's recorded counts up to (not including) its last SCP
+    iteration; returns the reference (X, U), the PIPG warm start of the last
+    iteration, and that iteration's sigma and PIPG count."""
+    nu = int(p["nu"])
+    X, U = init_guess(p, N, x0)
+    ws = PDState(N, nu)
+    for j in range(scp_iters - 1):
+        scp_iterate(p, x0, X, U, ws, force_pow=int(trace[j][0]), force_pipg=int(trace[j][1]))
+    A, Bm, Bp, xp = discretize(p, X, U)
+    qp = scale(p, x0, X, U, A, Bm, Bp, xp)
+    sig, _ = power(p, qp, ws, force_iters=int(trace[scp_iters - 1][0]))
+    return X, U, ws, sig, int(trace[scp_iters - 1][1])
+
+
+def final_iteration_outputs(p, x0, X, U, ws: PDState, sigma, n_pipg):
+    """The last SCP iteration as a function of x0 (the reference's first node
+    moving with it): returns (fuel, touchdown error) of its updated trajectory."""
+    X = X.copy(); U = U.copy(); w = ws.copy()
+    X[0, :14] = x0
+    scp_iterate(p, x0, X, U, w, force_pow=1, force_pipg=n_pipg, force_sigma=sigma)
+    return X[0, 0] - X[-1, 0], touchdown(p, X, U)
 
 
 def solve(p, N, x0, trace: Optional[np.ndarray] = None, replay_scp: int = 0):

@@ -20,7 +20,7 @@
 #include <string>
 
 #include "../../include/pdg_mc.h"
-#include "pdg_phases.cuh"
+#include "pdg_adjoint.cuh"
 
 using namespace pdg;
 
@@ -90,7 +90,7 @@ template <typename R, int NU>
 __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
              double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
-             int* trace, int* queue) {
+             int* trace, int* queue, double* rec, int rec_stride) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
   __shared__ int inst;
@@ -121,12 +121,20 @@ k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
     long long ptot = 0;
     for (j = 1; j <= P.scp_jmax; ++j) {
       if (P.budget_ns > 0.0 && double(globaltimer_ns() - t_start) > P.budget_ns) { stat = PDG_BUDGET; --j; break; }
+      double* rc = rec ? rec + (size_t)b * rec_stride : nullptr;
+      const int ow = N * (NX + NU), nw = L.img - L.xh;
+      if (rc) {  // reference and warm start of this SCP iteration (the last one is kept)
+        for (int t = threadIdx.x; t < N * NX; t += blockDim.x) rc[t] = double(sm[L.Xb + t]);
+        for (int t = threadIdx.x; t < N * NU; t += blockDim.x) rc[N * NX + t] = double(sm[L.Ub + t]);
+        for (int t = threadIdx.x; t < nw; t += blockDim.x) rc[ow + t] = double(sm[L.xh + t]);
+      }
       const R defect = phase_discretize<R, NU>(P, L, sm);
       phase_scale_extra<R, NU>(P, L, sm);
       __syncthreads();
       int pit;
       const R sigma = phase_power<R, NU>(P, L, sm, 0, &pit);
       const int jit = phase_pipg<R, NU>(P, L, sm, sigma, 0);
+      if (rc && threadIdx.x == 0) { rc[ow + nw] = double(sigma); rc[ow + nw + 1] = double(jit); }
       bool bad;
       const R step = phase_update<R, NU>(P, L, sm, &bad);
       ptot += jit;
@@ -359,6 +367,126 @@ __global__ void k_pack(int B, int Nmax, int threads, const double* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// gradient of the last SCP iteration (see pdg_adjoint.cuh), FP64
+// ---------------------------------------------------------------------------
+template <int NU>
+__global__ void __launch_bounds__(256, 1)
+k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
+       const double* __restrict__ rec, int rec_stride, const int* __restrict__ status,
+       const double* __restrict__ gf_in, const double* __restrict__ gt_in, double* ck, long long ck_stride,
+       int nck_max, double* grad, double* fuel_out, double* touch_out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sm = reinterpret_cast<double*>(smraw);
+  const int b = blockIdx.x;
+  const int N = Ns ? Ns[b] : Nmax;
+  const int st = status[b];
+  if (N < 2 || N > Nmax || !(st == PDG_CONVERGED || st == PDG_MAX_SCP)) {
+    if (threadIdx.x < 14) grad[(size_t)b * 14 + threadIdx.x] = 0.0;
+    if (threadIdx.x == 0) {
+      if (fuel_out) fuel_out[b] = 0.0;
+      if (touch_out) touch_out[b] = 0.0;
+    }
+    return;
+  }
+  const Lay L = make_lay(N, NU, blockDim.x);
+  const AdjLay AL = make_adj(L, NU, blockDim.x);
+  const double gf = gf_in ? gf_in[b] : 0.0, gt = gt_in ? gt_in[b] : 0.0;
+  const double* rc = rec + (size_t)b * rec_stride;
+  const int ow = N * (NX + NU), nw = L.img - L.xh;
+  load_x0<double>(L, sm, x0, b);
+  for (int t = threadIdx.x; t < N * NX; t += blockDim.x) sm[L.Xb + t] = rc[t];
+  for (int t = threadIdx.x; t < N * NU; t += blockDim.x) sm[L.Ub + t] = rc[N * NX + t];
+  for (int t = threadIdx.x; t < nw; t += blockDim.x) sm[L.xh + t] = rc[ow + t];
+  for (int t = threadIdx.x; t < AL.total - AL.Sb; t += blockDim.x) sm[AL.Sb + t] = 0.0;
+  const double sigma = rc[ow + nw];
+  const int n = int(rc[ow + nw + 1]);
+  __syncthreads();
+  phase_discretize<double, NU>(P, L, sm);
+  phase_scale_extra<double, NU>(P, L, sm);
+  __syncthreads();
+  const int ss = AL.ss;
+  double* state = sm + L.xt;
+  {
+    const int nx = N * NX, nuu = N * NU, nm = (N - 1) * NX;
+    for (int t = threadIdx.x; t < nx + nuu + 2 * nm + (N - 1); t += blockDim.x) {
+      if (t < nx) sm[L.xt + t] = sm[L.xh + t];
+      else if (t < nx + nuu) sm[L.ut + t - nx] = sm[L.uh + t - nx];
+      else if (t < nx + nuu + nm) { const int q = t - nx - nuu; sm[L.nup + q] = sm[L.mup + q]; sm[L.num + q] = sm[L.mum + q]; }
+      else if (t < nx + nuu + 2 * nm) { const int q = t - nx - nuu - nm; sm[L.vph + q] = sm[L.phi + q]; }
+      else { const int q = t - nx - nuu - 2 * nm; sm[L.vth + q] = sm[L.th + q]; }
+    }
+  }
+  __syncthreads();
+  const double wp = P.w_prox;
+  const double alpha = 2.0 / (wp + sqrt(wp * wp + 4.0 * P.omega * sigma));
+  const double beta = P.omega * alpha;
+  const double c1 = 1.0 - alpha * wp;
+  const double rho = P.rho;
+  double* ckb = ck + (size_t)b * ck_stride;
+  double* seg = ckb + (size_t)nck_max * ss;
+  const int nck = (n + 49) / 50;
+  // forward pass of the final PIPG loop with a checkpoint every 50 iterations
+  for (int j = 0; j < n; ++j) {
+    if (j % 50 == 0) {
+      for (int t = threadIdx.x; t < ss; t += blockDim.x) ckb[(size_t)(j / 50) * ss + t] = state[t];
+      __syncthreads();
+    }
+    grad_pipg_iter<NU>(P, L, AL, sm, alpha, beta, c1, rho, true);
+  }
+  // updated trajectory and the output functionals
+  for (int t = threadIdx.x; t < N * NX; t += blockDim.x) sm[AL.Xo + t] = sm[L.Xb + t] + P.Px[t % NX] * sm[L.xh + t];
+  for (int t = threadIdx.x; t < N * NU; t += blockDim.x) sm[AL.Uo + t] = sm[L.Ub + t] + P.Pu[t % NU] * sm[L.uh + t];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gdir[14];
+    for (int i = 0; i < 14; ++i) gdir[i] = 0.0;
+    const double fu = sm[AL.Xo + IM] - sm[AL.Xo + (N - 1) * NX + IM];
+    gdir[IM] += gf;                                      // m_1 = m_wet
+    sm[AL.xob + (N - 1) * NX + IM] += -gf * P.Px[IM];    // m_N through x_hat_N
+    const double e = touchdown_and_reverse<NU>(P, L, AL, sm, gt, gdir);
+    for (int i = 0; i < 14; ++i) sm[AL.gacc + i] = gdir[i];
+    if (fuel_out) fuel_out[b] = fu;
+    if (touch_out) touch_out[b] = e;
+  }
+  __syncthreads();
+  // reverse pass, segment by segment
+  double accA[NX], accBm[NU], accBp[NU], accW = 0.0;
+  for (int i = 0; i < NX; ++i) accA[i] = 0.0;
+  for (int i = 0; i < NU; ++i) { accBm[i] = 0.0; accBp[i] = 0.0; }
+  for (int sgm = nck - 1; sgm >= 0; --sgm) {
+    const int j0 = sgm * 50, j1 = min(n, j0 + 50);
+    for (int t = threadIdx.x; t < ss; t += blockDim.x) state[t] = ckb[(size_t)sgm * ss + t];
+    __syncthreads();
+    for (int j = j0; j < j1; ++j) {
+      for (int t = threadIdx.x; t < ss; t += blockDim.x) seg[(size_t)(j - j0) * ss + t] = state[t];
+      __syncthreads();
+      grad_pipg_iter<NU>(P, L, AL, sm, alpha, beta, c1, rho, true);
+    }
+    for (int j = j1 - 1; j >= j0; --j) {
+      for (int t = threadIdx.x; t < ss; t += blockDim.x) state[t] = seg[(size_t)(j - j0) * ss + t];
+      __syncthreads();
+      grad_pipg_iter<NU>(P, L, AL, sm, alpha, beta, c1, rho, false);
+      grad_pipg_reverse<NU>(P, L, AL, sm, alpha, beta, c1, rho, j == n - 1, accA, accBm, accBp, accW);
+    }
+  }
+  // cotangents of the first interval's blocks, unscaled
+  if (threadIdx.x < NX) {
+    const int i = threadIdx.x;
+    for (int c = 0; c < NX; ++c) sm[AL.cA + i * NX + c] = accA[c] * P.Px[c] * P.Pxinv[i];
+    for (int c = 0; c < NU; ++c) {
+      sm[AL.cBm + i * NU + c] = accBm[c] * P.Pu[c] * P.Pxinv[i];
+      sm[AL.cBp + i * NU + c] = accBp[c] * P.Pu[c] * P.Pxinv[i];
+    }
+    sm[AL.cw + i] = accW * P.Pxinv[i];
+  }
+  __syncthreads();
+  tangent_first_interval<NU>(P, L, AL, sm);
+  __syncthreads();
+  if (threadIdx.x < 14) grad[(size_t)b * 14 + threadIdx.x] = sm[AL.gacc + threadIdx.x];
+}
+
+
 // FMA-chain probe for the roofline denominator: every thread runs 8
 // independent dependency chains of `iters` FMAs each (16 flops per step).
 template <typename R>
@@ -403,6 +531,11 @@ struct pdg_handle {
   size_t lit_count = 0;
   int* pinned_done = nullptr;
   cudaStream_t cap = nullptr;  // plain form runs (and is captured) here
+  // gradient workspace
+  double* rec_ptr = nullptr;   // set only while a gradient solve runs
+  int rec_stride = 0;
+  void* gws = nullptr;
+  size_t gws_bytes = 0;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // host-buffer API staging
   void* stage = nullptr;
@@ -542,7 +675,7 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
     PDG_CUDA(h, cudaMemsetAsync(queue, 0, sizeof(int), s));
     const int grid = (int)((long long)occ * h->num_sms < B ? (long long)occ * h->num_sms : B);
     k_persistent<R, NU><<<grid, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, X, U, tf, fuel, status, scp_iters, pipg_iters,
-                                              trace, queue);
+                                              trace, queue, h->rec_ptr, h->rec_stride);
     PDG_CUDA(h, cudaGetLastError());
     return 0;
   }
@@ -754,6 +887,55 @@ static int run_noalloc(pdg_handle* h, int B, const double* x0, const int* Ns, do
   return 0;
 }
 
+template <int NU>
+static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const double* gf, const double* gt,
+                    double* grad, double* fuel_out, double* touch_out, int* status_out, cudaStream_t s) {
+  const int Tg = 256;
+  const Lay Lg = make_lay(h->n_max, NU, Tg);
+  const AdjLay Ag = make_adj(Lg, NU, Tg);
+  const size_t smem_g = (size_t)Ag.total * sizeof(double);
+  if (smem_g > 232448) return fail(h, PDG_EINVAL, "gradient kernel does not fit in shared memory for this n_max");
+  if (h->p.rk4_substeps > 32) return fail(h, PDG_EINVAL, "gradients support at most 32 RK4 substeps");
+  const int rec_stride = h->n_max * (NX + NU) + (Lg.img - Lg.xh) + 2;
+  const int ss = Ag.ss;
+  const int nck_max = (h->p.pipg_jmax + 49) / 50;
+  const long long ck_stride = (long long)(nck_max + 50) * ss;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t bX = sizeof(double) * (size_t)B * h->n_max * NX, bU = sizeof(double) * (size_t)B * h->n_max * NU;
+  const size_t bB = sizeof(double) * B, bI = sizeof(int) * B, bL = sizeof(long long) * B;
+  const size_t bR = sizeof(double) * (size_t)B * rec_stride, bC = sizeof(double) * (size_t)B * ck_stride;
+  const size_t need = al(bX) + al(bU) + 2 * al(bB) + 2 * al(bI) + al(bL) + al(bR) + al(bC);
+  if (h->gws_bytes < need) {
+    if (h->gws) cudaFree(h->gws);
+    h->gws = nullptr;
+    h->gws_bytes = 0;
+    PDG_CUDA(h, cudaMalloc(&h->gws, need));
+    h->gws_bytes = need;
+  }
+  char* c = (char*)h->gws;
+  double* X = (double*)c; c += al(bX);
+  double* U = (double*)c; c += al(bU);
+  double* tf = (double*)c; c += al(bB);
+  double* fu = (double*)c; c += al(bB);
+  int* st = (int*)c; c += al(bI);
+  int* sc = (int*)c; c += al(bI);
+  long long* pi = (long long*)c; c += al(bL);
+  double* rec = (double*)c; c += al(bR);
+  double* ck = (double*)c;
+  h->rec_ptr = rec;
+  h->rec_stride = rec_stride;
+  int rc = run_solve<double, NU>(h, B, x0, Ns, 1, X, U, tf, fu, st, sc, pi, nullptr, s);
+  h->rec_ptr = nullptr;
+  h->rec_stride = 0;
+  if (rc) return rc;
+  PDG_CUDA(h, cudaFuncSetAttribute(k_grad<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g));
+  k_grad<NU><<<B, Tg, smem_g, s>>>(h->dp, B, h->n_max, x0, Ns, rec, rec_stride, st, gf, gt, ck, ck_stride, nck_max,
+                                   grad, fuel_out, touch_out);
+  PDG_CUDA(h, cudaGetLastError());
+  if (status_out) PDG_CUDA(h, cudaMemcpyAsync(status_out, st, sizeof(int) * B, cudaMemcpyDeviceToDevice, s));
+  return 0;
+}
+
 #define PDG_DISPATCH(h, fn, ...)                                         \
   ((h)->p.precision == 0                                                 \
        ? ((h)->p.nu == 4 ? fn<double, 4>(__VA_ARGS__) : fn<double, 7>(__VA_ARGS__)) \
@@ -793,6 +975,7 @@ void pdg_mc_destroy(pdg_handle* h) {
   if (h->ints) cudaFree(h->ints);
   if (h->lit) cudaFree(h->lit);
   if (h->stage) cudaFree(h->stage);
+  if (h->gws) cudaFree(h->gws);
   if (h->pinned_done) cudaFreeHost(h->pinned_done);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -833,6 +1016,7 @@ int pdg_mc_solve_batch_host(pdg_handle* h, int B, const double* x0, const int* n
   const size_t need = al(bx0) + al(bN) + al(bX) + al(bU) + 2 * al(bs) + 2 * al(bi) + al(bl);
   if (h->stage_bytes < need) {
     if (h->stage) cudaFree(h->stage);
+  if (h->gws) cudaFree(h->gws);
     h->stage = nullptr;
     h->stage_bytes = 0;
     PDG_CUDA(h, cudaMalloc(&h->stage, need));
@@ -915,6 +1099,21 @@ int pdg_mc_solve_batch_noalloc(pdg_handle* h, int B, const double* x0, const int
   PDG_CUDA(h, cudaSetDevice(h->device));
   return PDG_DISPATCH(h, run_noalloc, h, B, x0, n_nodes, X, U, tf, fuel, status, scp_iters, pipg_iters,
                       (cudaStream_t)cuda_stream);
+}
+
+int pdg_mc_grad_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes, const double* dL_dfuel,
+                      const double* dL_dtouch, double* grad_x0, double* fuel, double* touch, int* status,
+                      void* cuda_stream) {
+  if (!h) return PDG_EINVAL;
+  h->err.clear();
+  if (B < 0) return fail(h, PDG_EINVAL, "B must be >= 0");
+  if (B == 0) return PDG_OK;
+  if (!x0 || !grad_x0) return fail(h, PDG_EINVAL, "NULL buffer");
+  if (h->p.precision != 0) return fail(h, PDG_EINVAL, "gradients are computed in FP64 only (precision 0)");
+  PDG_CUDA(h, cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  return h->p.nu == 4 ? run_grad<4>(h, B, x0, n_nodes, dL_dfuel, dL_dtouch, grad_x0, fuel, touch, status, s)
+                      : run_grad<7>(h, B, x0, n_nodes, dL_dfuel, dL_dtouch, grad_x0, fuel, touch, status, s);
 }
 
 int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream) {

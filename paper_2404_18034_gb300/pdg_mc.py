@@ -22,7 +22,8 @@ PDG_CONVERGED, PDG_MAX_SCP, PDG_NONFINITE, PDG_BUDGET, PDG_BAD_INPUT = 0, 1, 2, 
 ERRORS = {-1: "PDG_EINVAL", -2: "PDG_ENOMEM", -3: "PDG_ECUDA"}
 EXPORTS = ("pdg_mc_init", "pdg_mc_destroy", "pdg_mc_last_error", "pdg_mc_solve_batch",
            "pdg_mc_solve_batch_host", "pdg_mc_subproblem", "pdg_mc_scp_step", "pdg_mc_launch_info",
-           "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc")
+           "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc",
+           "pdg_mc_grad_batch")
 
 
 class PdgParams(C.Structure):
@@ -72,8 +73,9 @@ def load_library(path: str = LIB_PATH):
     L.pdg_mc_set_threads.argtypes = [_VP, C.c_int]
     L.pdg_mc_probe_fma.argtypes = [C.c_int, C.POINTER(C.c_double), _VP]
     L.pdg_mc_solve_batch_noalloc.argtypes = [_VP, C.c_int, _VP, _VP] + [_VP] * 7 + [_VP]
+    L.pdg_mc_grad_batch.argtypes = [_VP, C.c_int] + [_VP] * 8 + [_VP]
     for name in ("pdg_mc_init", "pdg_mc_solve_batch", "pdg_mc_solve_batch_host", "pdg_mc_subproblem",
-                 "pdg_mc_scp_step", "pdg_mc_launch_info", "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc"):
+                 "pdg_mc_scp_step", "pdg_mc_launch_info", "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc", "pdg_mc_grad_batch"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -203,6 +205,19 @@ class Solver:
                                                  self._stream(stream))
         self._check(rc, "pdg_mc_solve_batch_noalloc")
         return out
+
+    def grad(self, x0, n_nodes=None, dL_dfuel=None, dL_dtouch=None, stream=None):
+        """pdg_mc_grad_batch: returns grad (B x 14), fuel, touch, status."""
+        import torch
+        B = int(x0.shape[0])
+        f = dict(dtype=torch.float64, device=x0.device)
+        o = dict(grad=torch.empty(B, 14, **f), fuel=torch.empty(B, **f), touch=torch.empty(B, **f),
+                 status=torch.empty(B, dtype=torch.int32, device=x0.device))
+        rc = self.lib.pdg_mc_grad_batch(self.h, B, _ptr(x0), _ptr(n_nodes), _ptr(dL_dfuel), _ptr(dL_dtouch),
+                                        _ptr(o["grad"]), _ptr(o["fuel"]), _ptr(o["touch"]), _ptr(o["status"]),
+                                        self._stream(stream))
+        self._check(rc, "pdg_mc_grad_batch")
+        return o
 
     def solve_host(self, x0: np.ndarray, n_nodes: Optional[np.ndarray] = None, mode: int = 1, out=None,
                    stream=None):

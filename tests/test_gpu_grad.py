@@ -1,0 +1,76 @@
+"""Adjoint gradients (pdg_mc_grad_batch) against central finite differences
+(h = 1e-6) of the oracle's last SCP iteration as a function of x0, replayed at
+the GPU's recorded counts and step size."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_18034_gb300 import build
+    build.build()
+    return torch
+
+
+def _fd(oracle, p, x0, X, U, ws, sig, n, h=1e-6):
+    g = np.zeros((14, 2))
+    for j in range(14):
+        e = np.zeros(14); e[j] = h
+        fp = np.array(oracle.final_iteration_outputs(p, x0 + e, X, U, ws, sig, n))
+        fm = np.array(oracle.final_iteration_outputs(p, x0 - e, X, U, ws, sig, n))
+        g[j] = (fp - fm) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("nu,N,B", [(4, 15, 6), (4, 10, 3), (7, 12, 2)])
+def test_gradient_matches_oracle_finite_differences(torch_cuda, oracle, inputs, nu, N, B):
+    torch = torch_cuda
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    p = inputs.load_params(nu=nu)
+    S = Solver(p, N)
+    x0 = inputs.dispersion(p, B, inputs.config_seed(3), "bj")
+    d = torch.from_numpy(x0).cuda()
+    sol = S.solve(d, mode=1, trace=True)
+    ones = torch.ones(B, dtype=torch.float64, device="cuda")
+    zeros = torch.zeros_like(ones)
+    gfu = S.grad(d, None, ones, zeros)
+    gtd = S.grad(d, None, zeros, ones)
+    torch.cuda.synchronize()
+    tr = sol["trace"].cpu().numpy()
+    sc = sol["scp_iters"].cpu().numpy()
+    st = sol["status"].cpu().numpy()
+    np.testing.assert_array_equal(gfu["status"].cpu().numpy(), st)
+    np.testing.assert_allclose(gfu["fuel"].cpu().numpy(), sol["fuel"].cpu().numpy(), rtol=1e-12, atol=1e-12)
+    for b in range(B):
+        if st[b] not in (0, 1):
+            continue
+        X, U, ws, sig, n = oracle.final_iteration_state(p, N, x0[b], tr[b], int(sc[b]))
+        fd = _fd(oracle, p, x0[b], X, U, ws, sig, n)
+        g1 = gfu["grad"][b].cpu().numpy()
+        g2 = gtd["grad"][b].cpu().numpy()
+        assert np.all(np.abs(g1 - fd[:, 0]) <= 1e-6 + 1e-5 * np.abs(fd[:, 0])), (b, g1, fd[:, 0])
+        assert np.all(np.abs(g2 - fd[:, 1]) <= 1e-9 + 1e-4 * np.abs(fd[:, 1])), (b, g2, fd[:, 1])
+        f0, t0 = oracle.final_iteration_outputs(p, x0[b], X, U, ws, sig, n)
+        assert abs(gtd["touch"][b].item() - t0) <= 1e-9 + 1e-6 * abs(t0)
+    S.close()
+
+
+def test_autograd_function(torch_cuda, inputs):
+    torch = torch_cuda
+    from paper_2404_18034_gb300.autograd import pdg_outputs
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    p = inputs.load_params()
+    S = Solver(p, 10)
+    x0 = torch.from_numpy(inputs.dispersion(p, 4, 17, "bj")).cuda().requires_grad_(True)
+    fuel, touch = pdg_outputs(x0, S)
+    (fuel.sum() + 3.0 * touch.sum()).backward()
+    ref = S.grad(x0.detach(), None, torch.ones(4, dtype=torch.float64, device="cuda"),
+                 3.0 * torch.ones(4, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(x0.grad.cpu().numpy(), ref["grad"].cpu().numpy(), rtol=1e-12, atol=1e-15)
+    S.close()
