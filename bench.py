@@ -42,10 +42,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--mode", default="persistent", choices=["persistent", "plain"])
+    ap.add_argument("--mode", default="persistent", choices=["persistent", "plain", "classed"])
     ap.add_argument("--batch", type=int, default=16384)
     ap.add_argument("--nodes", type=int, default=15)
-    ap.add_argument("--dispersion", default="bj")
+    ap.add_argument("--dispersion", default="bj", choices=["bj", "paper256", "nominal"])
+    ap.add_argument("--nu", type=int, default=4, choices=[4, 7], help="7: the paper's model with the RCS torque")
     ap.add_argument("--uneven", action="store_true", help="N per instance uniform in {10, 15, 20, 30}")
     ap.add_argument("--grad", action="store_true", help="time gradients (pdg_mc_grad_batch) instead of solves")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic)")
@@ -56,7 +57,8 @@ def parse():
 
 def workload_name(a):
     n = "Nuneven10-30" if a.uneven else f"N{a.nodes}"
-    return f"pdg6dof_{a.dispersion}_B{a.batch}_{n}_{a.precision}_{a.mode}"
+    nu = "" if a.nu == 4 else f"_nu{a.nu}"
+    return f"pdg6dof_{a.dispersion}_B{a.batch}_{n}{nu}_{a.precision}_{a.mode}"
 
 
 class ClockSampler:
@@ -230,7 +232,7 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     prec = 0 if a.precision == "fp64" else 1
-    p = inputs.load_params()
+    p = inputs.load_params(nu=a.nu)
     seed = inputs.config_seed(2) + 1000 * rank
     x0h = inputs.dispersion(p, a.batch, seed, a.dispersion)
     x0 = torch.from_numpy(x0h).to(dev)
@@ -238,7 +240,7 @@ def run_ours(a):
     Ns = torch.from_numpy(Ns_h).to(dev) if a.uneven else None
     if a.uneven:
         a.nodes = int(Ns_h.max())
-    mode = 1 if a.mode == "persistent" else 0
+    mode = {"plain": 0, "persistent": 1, "classed": 2}[a.mode]
     from paper_2404_18034_gb300.autotune import DEFAULT_CACHE
     S = Solver(p, a.nodes, prec, tune_cache=DEFAULT_CACHE, mode=mode)
     out = S.alloc_outputs(a.batch, dev)
@@ -329,7 +331,8 @@ def run_ours(a):
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline(p, a, inputs.config_seed(2), a.cpu_sample)
 
-    launches = a.steps * (1 if mode == 1 else 1 + 4 * int(scp.max()))
+    launches = a.steps * (1 if mode == 1 else (1 + 4 * int(scp.max()) if mode == 0 else 1 + len(set(Ns_h.tolist()))
+                                                if a.uneven else 1))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
@@ -347,7 +350,7 @@ def run_ours(a):
             "mean_scp_iters": float(scp.mean()), "mean_pipg_iters_per_solve": float(pipg.mean()),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                          "frac": achieved / peak_nominal, "traffic": None,
-                         "kernel": "k_persistent" if mode == 1 else "whole plain-form step",
+                         "kernel": "whole plain-form step" if mode == 0 else "k_persistent",
                          "flops_per_launch": fl,
                          "peak_source": f"derived: {SMS} SMs x {FMA_PER_CLK[a.precision]} "
                                         f"{a.precision.upper()} FMA/clk x 2 flop x {MAX_SM_MHZ:.0f} MHz",

@@ -91,7 +91,12 @@ const char* pdg_mc_last_error(const pdg_handle* h);
  *   mode      0: plain form, one launch per phase per SCP iteration, the
  *                iteration captured once in a CUDA graph and replayed;
  *             1: persistent form, one launch, each CTA takes instances from
- *                a work queue until none is left.
+ *                a work queue until none is left;
+ *             2: persistent form by shape class: the instances are sorted by
+ *                node count on the device and every node count gets its own
+ *                persistent grid (shared memory and CTA size for that count),
+ *                all grids running concurrently on forked streams.  Same as
+ *                mode 1 when n_nodes is NULL.
  *   X, U      device outputs (see layouts)
  *   tf, fuel  device [B]: final time sum_k dtau (s_k + s_{k+1})/2 and m_1 - m_N
  *   status    device [B] PDG_CONVERGED ... PDG_BAD_INPUT

@@ -90,16 +90,20 @@ template <typename R, int NU>
 __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
 k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
              double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
-             int* trace, int* queue, double* rec, int rec_stride) {
+             int* trace, int* queue, double* rec, int rec_stride, const int* perm, const int* class_off, int cls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
   __shared__ int inst;
+  // shape-class launch: this grid serves the instances perm[class_off[cls] ..
+  // class_off[cls + 1]) (all of one node count)
+  const int nq = perm ? class_off[cls + 1] - class_off[cls] : B;
   for (;;) {
     if (threadIdx.x == 0) inst = atomicAdd(queue, 1);
     __syncthreads();
-    const int b = inst;
+    const int qi = inst;
     __syncthreads();
-    if (b >= B) break;
+    if (qi >= nq) break;
+    const int b = perm ? perm[class_off[cls] + qi] : qi;
     const int N = Ns ? Ns[b] : Nmax;
     if (N < 2 || N > Nmax) {
       Lay L0 = make_lay(2, NU, blockDim.x);
@@ -487,6 +491,30 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
 }
 
 
+// Counting sort of the instance ids by node count (shape classes 0..32):
+// class_off[c] .. class_off[c+1] index perm for N = c.  One CTA.
+__global__ void k_class_sort(int B, const int* __restrict__ Ns, int n_max, int* perm, int* class_off) {
+  __shared__ int cnt[NMAX + 2], off[NMAX + 2];
+  for (int i = threadIdx.x; i < NMAX + 2; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    int N = Ns[b];
+    if (N < 2 || N > n_max) N = n_max;  // bad inputs go with the largest class and are rejected there
+    atomicAdd(&cnt[N], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int c = 0; c <= NMAX + 1; ++c) { off[c] = o; class_off[c] = o; o += (c <= NMAX ? cnt[c] : 0); }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    int N = Ns[b];
+    if (N < 2 || N > n_max) N = n_max;
+    perm[atomicAdd(&off[N], 1)] = b;
+  }
+}
+
 // FMA-chain probe for the roofline denominator: every thread runs 8
 // independent dependency chains of `iters` FMAs each (16 flops per step).
 template <typename R>
@@ -532,6 +560,10 @@ struct pdg_handle {
   int* pinned_done = nullptr;
   cudaStream_t cap = nullptr;  // plain form runs (and is captured) here
   // gradient workspace
+  int* cls = nullptr;          // shape classes: perm, class offsets, queues
+  size_t cls_count = 0;
+  cudaStream_t cls_streams[NMAX + 1] = {};
+  cudaEvent_t cls_events[NMAX + 1] = {};
   double* rec_ptr = nullptr;   // set only while a gradient solve runs
   int rec_stride = 0;
   void* gws = nullptr;
@@ -626,14 +658,24 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
 }
 
 
-// Threads per CTA: one thread per dual row of the largest instance (whole
-// warps) plus the warp of CTCS rows, within [128, 512].
-static int pick_threads(const pdg_handle* h) {
-  if (h->threads_override > 0) return h->threads_override;
-  int t = round32((h->n_max - 1) * 15) + 32;
+// Threads per CTA for instances of N nodes: one thread per dual row (whole
+// warps) plus the warp of CTCS rows; in FP64, when three CTAs fit on an SM by
+// shared memory, half of that (more CTAs per SM keep the FP64 pipe busier).
+// Within [128, 512].
+static int threads_for(int N, int nu, int precision) {
+  int t = round32((N - 1) * 15) + 32;
+  if (precision == 0) {
+    const Lay L = make_lay(N, nu, t);
+    if ((size_t)L.total * 8 * 3 <= 227 * 1024) t = round32(round32((N - 1) * 15) / 2) + 32;
+  }
   if (t > 512) t = 512;
   if (t < 128) t = 128;
   return t;
+}
+
+static int pick_threads(const pdg_handle* h) {
+  if (h->threads_override > 0) return h->threads_override;
+  return threads_for(h->n_max, h->p.nu, h->p.precision);
 }
 
 template <typename R, int NU>
@@ -671,12 +713,56 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
     h->ints_count = nints;
   }
   int* queue = h->ints + 4 * (size_t)B + 1;
-  if (mode == 1) {
+  if (mode == 1 || (mode == 2 && !Ns)) {
     PDG_CUDA(h, cudaMemsetAsync(queue, 0, sizeof(int), s));
     const int grid = (int)((long long)occ * h->num_sms < B ? (long long)occ * h->num_sms : B);
     k_persistent<R, NU><<<grid, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, X, U, tf, fuel, status, scp_iters, pipg_iters,
-                                              trace, queue, h->rec_ptr, h->rec_stride);
+                                              trace, queue, h->rec_ptr, h->rec_stride, nullptr, nullptr, 0);
     PDG_CUDA(h, cudaGetLastError());
+    return 0;
+  }
+  if (mode == 2) {
+    // shape classes: one persistent grid per node count, all on forked streams
+    const size_t ncls = NMAX + 2;
+    if (h->cls_count < (size_t)B + ncls + NMAX + 1) {
+      if (h->cls) cudaFree(h->cls);
+      h->cls = nullptr;
+      h->cls_count = 0;
+      PDG_CUDA(h, cudaMalloc(&h->cls, sizeof(int) * ((size_t)B + ncls + NMAX + 1)));
+      h->cls_count = (size_t)B + ncls + NMAX + 1;
+    }
+    int* perm = h->cls;
+    int* class_off = h->cls + B;
+    int* queues = class_off + ncls;
+    if (!h->ev_in) PDG_CUDA(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    PDG_CUDA(h, cudaMemsetAsync(queues, 0, sizeof(int) * (NMAX + 1), s));
+    k_class_sort<<<1, 1024, 0, s>>>(B, Ns, h->n_max, perm, class_off);
+    PDG_CUDA(h, cudaGetLastError());
+    PDG_CUDA(h, cudaEventRecord(h->ev_in, s));
+    for (int N = h->n_max; N >= 2; --N) {
+      const int Tn = h->threads_override > 0 && N == h->n_max ? h->threads_override
+                                                               : threads_for(N, NU, h->p.precision);
+      const Lay Ln = make_lay(N, NU, Tn);
+      const size_t smem_n = (size_t)Ln.total * sizeof(R);
+      if (Ln.ipw < 1) continue;
+      int occ_n = 0;
+      PDG_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_n, k_persistent<R, NU>, Tn, smem_n));
+      if (occ_n < 1) return fail(h, PDG_EINVAL, "a shape class does not fit on an SM");
+      cudaStream_t cs = h->cls_streams[N];
+      if (!cs) {
+        PDG_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        h->cls_streams[N] = cs;
+        PDG_CUDA(h, cudaEventCreateWithFlags(&h->cls_events[N], cudaEventDisableTiming));
+      }
+      PDG_CUDA(h, cudaStreamWaitEvent(cs, h->ev_in, 0));
+      const int grid = (int)((long long)occ_n * h->num_sms < B ? (long long)occ_n * h->num_sms : B);
+      k_persistent<R, NU><<<grid, Tn, smem_n, cs>>>(h->dp, B, h->n_max, x0, Ns, X, U, tf, fuel, status, scp_iters,
+                                                    pipg_iters, trace, queues + N, h->rec_ptr, h->rec_stride, perm,
+                                                    class_off, N);
+      PDG_CUDA(h, cudaGetLastError());
+      PDG_CUDA(h, cudaEventRecord(h->cls_events[N], cs));
+      PDG_CUDA(h, cudaStreamWaitEvent(s, h->cls_events[N], 0));
+    }
     return 0;
   }
   // plain form
@@ -907,6 +993,11 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
   const size_t need = al(bX) + al(bU) + 2 * al(bB) + 2 * al(bI) + al(bL) + al(bR) + al(bC);
   if (h->gws_bytes < need) {
     if (h->gws) cudaFree(h->gws);
+  if (h->cls) cudaFree(h->cls);
+  for (int i = 0; i <= NMAX; ++i) {
+    if (h->cls_streams[i]) cudaStreamDestroy(h->cls_streams[i]);
+    if (h->cls_events[i]) cudaEventDestroy(h->cls_events[i]);
+  }
     h->gws = nullptr;
     h->gws_bytes = 0;
     PDG_CUDA(h, cudaMalloc(&h->gws, need));
@@ -976,6 +1067,11 @@ void pdg_mc_destroy(pdg_handle* h) {
   if (h->lit) cudaFree(h->lit);
   if (h->stage) cudaFree(h->stage);
   if (h->gws) cudaFree(h->gws);
+  if (h->cls) cudaFree(h->cls);
+  for (int i = 0; i <= NMAX; ++i) {
+    if (h->cls_streams[i]) cudaStreamDestroy(h->cls_streams[i]);
+    if (h->cls_events[i]) cudaEventDestroy(h->cls_events[i]);
+  }
   if (h->pinned_done) cudaFreeHost(h->pinned_done);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -992,7 +1088,7 @@ int pdg_mc_solve_batch(pdg_handle* h, int B, const double* x0, const int* n_node
   h->err.clear();
   if (B < 0) return fail(h, PDG_EINVAL, "B must be >= 0");
   if (B == 0) return PDG_OK;
-  if (mode != 0 && mode != 1) return fail(h, PDG_EINVAL, "mode must be 0 (plain) or 1 (persistent)");
+  if (mode < 0 || mode > 2) return fail(h, PDG_EINVAL, "mode must be 0 (plain), 1 (persistent) or 2 (persistent, shape classes)");
   if (!x0 || !X || !U || !tf || !fuel || !status || !scp_iters || !pipg_iters) return fail(h, PDG_EINVAL, "NULL buffer");
   PDG_CUDA(h, cudaSetDevice(h->device));
   return PDG_DISPATCH(h, run_solve, h, B, x0, n_nodes, mode, X, U, tf, fuel, status, scp_iters, pipg_iters, trace,
@@ -1017,6 +1113,11 @@ int pdg_mc_solve_batch_host(pdg_handle* h, int B, const double* x0, const int* n
   if (h->stage_bytes < need) {
     if (h->stage) cudaFree(h->stage);
   if (h->gws) cudaFree(h->gws);
+  if (h->cls) cudaFree(h->cls);
+  for (int i = 0; i <= NMAX; ++i) {
+    if (h->cls_streams[i]) cudaStreamDestroy(h->cls_streams[i]);
+    if (h->cls_events[i]) cudaEventDestroy(h->cls_events[i]);
+  }
     h->stage = nullptr;
     h->stage_bytes = 0;
     PDG_CUDA(h, cudaMalloc(&h->stage, need));
