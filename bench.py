@@ -30,6 +30,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "converged PDG SCP solves/s on 1 GB300, batch 16384, N=15; % FP64/FP32 peak"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the solve
+# kernel per instance, from ncu captures of the kernel sources with the given
+# hash (profiles/ has the summaries); reported only while the sources match.
+PROFILED_TRAFFIC = {
+    "353265547f3e6e43": {("fp64", 4, 15, "persistent"): 936.56e6 / 16384},
+}
+
+
+def kernel_source_hash() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2404_18034_gb300", "csrc", "*.cu*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 SMS = 152
 MAX_SM_MHZ = 2070.0
 FMA_PER_CLK = {"fp64": 2, "fp32": 128}  # per SM, GB300
@@ -53,6 +70,22 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
+
+
+def shard_seed(base_seed: int, rank: int) -> int:
+    """Each rank draws its own dispersed batch (weak scaling: no data exchange)."""
+    return base_seed + 1000 * rank
+
+
+def reduce_over_ranks(total_ms: float, converged: int, solved: int, dist, device):
+    """Whole-job figures: the slowest rank's time and the instances of all ranks."""
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    c = torch.tensor([converged, solved], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), int(c[0]), int(c[1])
 
 
 def workload_name(a):
@@ -233,7 +266,7 @@ def run_ours(a):
         dist.barrier()
     prec = 0 if a.precision == "fp64" else 1
     p = inputs.load_params(nu=a.nu)
-    seed = inputs.config_seed(2) + 1000 * rank
+    seed = shard_seed(inputs.config_seed(2), rank)
     x0h = inputs.dispersion(p, a.batch, seed, a.dispersion)
     x0 = torch.from_numpy(x0h).to(dev)
     Ns_h = inputs.node_counts(a.batch, seed) if a.uneven else None
@@ -277,15 +310,9 @@ def run_ours(a):
     pipg = out["pipg_iters"].cpu().numpy()
     pow_it = tr[:, :, 0].sum(1)
     total_ms = float(np.sum(ms))
-    stats = torch.tensor([total_ms, conv * a.steps, a.batch * a.steps], dtype=torch.float64, device=dev)
-    if world > 1:
-        t_max = stats[0:1].clone()
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        cnt = stats[1:].clone()
-        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
-        stats = torch.cat([t_max, cnt])
-    total_ms_max = float(stats[0])
-    value = float(stats[1]) / (total_ms_max * 1e-3)
+    total_ms_max, conv_all, solved_all = reduce_over_ranks(total_ms, conv * a.steps, a.batch * a.steps,
+                                                           dist if world > 1 else None, dev)
+    value = conv_all / (total_ms_max * 1e-3)
 
     # roofline of the dominant kernel (the persistent solve kernel is the whole step)
     fl = flops.solve_flops(Ns_h if a.uneven else np.full(a.batch, a.nodes), p["nu"], p["rk4_substeps"], scp, pow_it,
@@ -315,16 +342,11 @@ def run_ours(a):
             r = S.solve_host(x0_pinned, Ns_h, mode=mode, out=outs, stream=stream)
             e2e_conv += int(np.sum(r["status"] == 0))
         e2e_s = time.perf_counter() - t0
-        es = torch.tensor([e2e_s, e2e_conv], dtype=torch.float64, device=dev)
-        if world > 1:
-            t_max = es[0:1].clone()
-            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-            c = es[1:].clone()
-            dist.all_reduce(c, op=dist.ReduceOp.SUM)
-            es = torch.cat([t_max, c])
+        e2e_ms_max, e2e_conv_all, _ = reduce_over_ranks(1e3 * e2e_s, e2e_conv, a.batch * a.steps,
+                                                        dist if world > 1 else None, dev)
         h2d = x0h.nbytes + (Ns_h.nbytes if a.uneven else 0)
         d2h = sum(v.nbytes for v in outs.values())
-        e2e = {"value": float(es[1]) / float(es[0]), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": e2e_conv_all / (e2e_ms_max * 1e-3), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
@@ -346,10 +368,14 @@ def run_ours(a):
                        "threads_from_autotune_cache": S.tuned_threads is not None,
                        "smem_bytes_per_cta": info["smem_bytes"]},
             "converged_fraction": conv / a.batch,
-            "all_solves_per_s": float(stats[2]) / (total_ms_max * 1e-3),
+            "all_solves_per_s": solved_all / (total_ms_max * 1e-3),
             "mean_scp_iters": float(scp.mean()), "mean_pipg_iters_per_solve": float(pipg.mean()),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
-                         "frac": achieved / peak_nominal, "traffic": None,
+                         "frac": achieved / peak_nominal,
+                         "traffic": (PROFILED_TRAFFIC.get(kernel_source_hash(), {}).get(
+                             (a.precision, p["nu"], a.nodes, a.mode)) or 0) * a.batch or None,
+                         "traffic_algorithmic_bytes": int(x0h.nbytes + a.batch * a.nodes * (15 + p["nu"]) * 8
+                                                          + a.batch * 28),
                          "kernel": "whole plain-form step" if mode == 0 else "k_persistent",
                          "flops_per_launch": fl,
                          "peak_source": f"derived: {SMS} SMs x {FMA_PER_CLK[a.precision]} "
