@@ -159,6 +159,7 @@ int orc_g(const orc_params* p, const double* x, const double* u, double* g) {
   g[4] = dot3(w, w) - p->omega_max * p->omega_max;
   g[5] = nT - T[0] / cos(p->delta_max);
   g[6] = nT - p->T_max;
+  if (p->soc_thrust) { g[5] = -1.0; g[6] = -1.0; }  /* imposed by projection instead */
   g[7] = p->T_min - nT;
   if (p->nu == 7) {
     const double* gm = u + 3;
@@ -394,6 +395,7 @@ int orc_qp_alloc(orc_qp* qp, int N, int nu) {
   memset(qp, 0, sizeof *qp);
   qp->N = N;
   qp->nu = nu;
+  qp->Tbar = calloc((size_t)N * 3, sizeof(double));
   qp->Am = calloc((size_t)(N - 1) * NX * NX, sizeof(double));
   qp->Ap = calloc((size_t)(N - 1) * NX * NX, sizeof(double));
   qp->Bm = calloc((size_t)(N - 1) * NX * nu, sizeof(double));
@@ -402,12 +404,12 @@ int orc_qp_alloc(orc_qp* qp, int N, int nu) {
   qp->eps = calloc((size_t)(N - 1), sizeof(double));
   qp->umin = calloc((size_t)N * nu, sizeof(double));
   qp->umax = calloc((size_t)N * nu, sizeof(double));
-  return (qp->Am && qp->Ap && qp->Bm && qp->Bp && qp->w && qp->eps && qp->umin && qp->umax) ? 0 : -1;
+  return (qp->Tbar && qp->Am && qp->Ap && qp->Bm && qp->Bp && qp->w && qp->eps && qp->umin && qp->umax) ? 0 : -1;
 }
 
 void orc_qp_free(orc_qp* qp) {
   free(qp->Am); free(qp->Ap); free(qp->Bm); free(qp->Bp);
-  free(qp->w); free(qp->eps); free(qp->umin); free(qp->umax);
+  free(qp->w); free(qp->eps); free(qp->umin); free(qp->umax); free(qp->Tbar);
   memset(qp, 0, sizeof *qp);
 }
 
@@ -454,6 +456,12 @@ void orc_scale(const orc_params* p, int N, const double* x0, const double* X, co
     qp->ecost[i] = 0.0;
   }
   qp->ecost[XM] = -1.0; /* propellant-optimal: maximize m_N */
+  qp->soc = p->soc_thrust;
+  for (int k = 0; k < N; k++)
+    for (int i = 0; i < 3; i++) qp->Tbar[k * 3 + i] = U[k * nu + i];
+  qp->soc_Tmax = p->T_max;
+  qp->soc_tan = tan(p->delta_max);
+  qp->soc_PT = p->P_u[0];
   qp->w_cost = p->w_cost;
   qp->w_prox = p->w_prox;
   qp->w_ep = p->w_ep;
@@ -614,6 +622,37 @@ static int stop_custom(const orc_params* p, const orc_qp* qp, const orc_pd* a, c
 
 static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+void orc_sector_project(double* T, double Tmax, double tan_delta) {
+  /* cone K = {(t, z): ||z|| <= a t}, t = T_x, z = (T_y, T_z), a = tan(delta) */
+  double t = T[0], r = sqrt(T[1] * T[1] + T[2] * T[2]), a = tan_delta;
+  if (r > a * t) {
+    if (a * r <= -t) {
+      T[0] = T[1] = T[2] = 0.0;
+    } else {
+      double tp = (t + a * r) / (1.0 + a * a);
+      double rp = a * tp;
+      T[0] = tp;
+      T[1] = rp * T[1] / r;
+      T[2] = rp * T[2] / r;
+    }
+  }
+  /* then the ball of radius Tmax about the apex */
+  double n = sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+  if (n > Tmax) {
+    double f = Tmax / n;
+    T[0] *= f; T[1] *= f; T[2] *= f;
+  }
+}
+
+/* projection of node k's scaled thrust onto the sector (shifted by the
+ * reference and scaled by P_T) */
+static void soc_project_uhat(const orc_qp* qp, int k, double* uh) {
+  double T[3];
+  for (int i = 0; i < 3; i++) T[i] = qp->Tbar[k * 3 + i] + qp->soc_PT * uh[i];
+  orc_sector_project(T, qp->soc_Tmax, qp->soc_tan);
+  for (int i = 0; i < 3; i++) uh[i] = (T[i] - qp->Tbar[k * 3 + i]) / qp->soc_PT;
+}
+
 int orc_pipgc(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, int force_iters) {
   const int N = qp->N, nu = qp->nu;
   const double wp = qp->w_prox;
@@ -644,6 +683,7 @@ int orc_pipgc(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, i
     for (int c = 0; c < nu; c++) gu[c] = wp * ut[c];
     mtv_add(NX, nu, qp->Bm, vph, gu);
     for (int c = 0; c < nu; c++) cur.uh[c] = clampd(ut[c] - alpha * gu[c], qp->umin[c], qp->umax[c]);
+    if (qp->soc) soc_project_uhat(qp, 0, cur.uh);
     /* nodes 2..N-1 */
     for (int k = 1; k < N - 1; k++) {
       for (int i = 0; i < NX; i++) g[i] = wp * xt[k * NX + i];
@@ -656,6 +696,7 @@ int orc_pipgc(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, i
       mtv_add(NX, nu, qp->Bp + (k - 1) * NX * nu, vph + (k - 1) * NX, gu); /* R5 */
       for (int c = 0; c < nu; c++)
         cur.uh[k * nu + c] = clampd(ut[k * nu + c] - alpha * gu[c], qp->umin[k * nu + c], qp->umax[k * nu + c]);
+      if (qp->soc) soc_project_uhat(qp, k, cur.uh + k * nu);
     }
     /* node N */
     {
@@ -669,6 +710,7 @@ int orc_pipgc(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, i
       mtv_add(NX, nu, qp->Bp + (k - 1) * NX * nu, vph + (k - 1) * NX, gu);
       for (int c = 0; c < nu; c++)
         cur.uh[k * nu + c] = clampd(ut[k * nu + c] - alpha * gu[c], qp->umin[k * nu + c], qp->umax[k * nu + c]);
+      if (qp->soc) soc_project_uhat(qp, k, cur.uh + k * nu);
     }
     /* virtual controls (R4) */
     for (int i = 0; i < (N - 1) * NX; i++) {
@@ -832,6 +874,8 @@ void orc_pipg_generic(const orc_qp* qp, double alpha, double omega, double rho, 
       for (int r = 0; r < nh; r++) a += H[r * nz + i] * chi[r];
       z[i] = clampd(zeta[i] - alpha * a, lo[i], hi[i]);
     }
+    if (qp->soc)
+      for (int k = 0; k < N; k++) soc_project_uhat(qp, k, z + NX * N + k * nu);
     for (int i = 0; i < nz; i++) d[i] = 2.0 * z[i] - zeta[i];
     for (int r = 0; r < ng; r++) {
       double a = 0;

@@ -47,6 +47,8 @@ typedef struct orc_params {
   double scp_eps_step, scp_eps_defect;
   int rk4_substeps;
   double tf_guess;        /* initial guess of the final time */
+  int soc_thrust;         /* 1: T_max and gimbal bounds as a per-node second-order-cone
+                             projection in PIPG instead of CTCS rows */
 } orc_params;
 
 /* Scaled convex subproblem data (Eq. cvx-subproblem-custom). */
@@ -65,6 +67,9 @@ typedef struct orc_qp {
   int fixf[15];
   double w_cost, w_prox, w_ep;
   double ecost[15]; /* e_cost on the scaled x_N (Sec. 4 objective) */
+  int soc;          /* thrust sector projection on (see orc_params.soc_thrust) */
+  double *Tbar;     /* [N][3] reference thrust (unscaled) */
+  double soc_Tmax, soc_tan, soc_PT;
 } orc_qp;
 
 /* PIPG primal-dual state (warm start in, solution out), Alg. PIPG_custom. */
@@ -117,6 +122,10 @@ void orc_pipg_generic(const orc_qp* qp, double alpha, double omega, double rho, 
                       double* zout, double* wout, double* vout);
 void orc_z_pack(const orc_qp* qp, const orc_pd* s, double* z);
 void orc_z_unpack(const orc_qp* qp, const double* z, orc_pd* s);
+
+/* Euclidean projection of T onto {||T|| <= Tmax, ||(T_y, T_z)|| <= tan_delta T_x}
+ * (second-order cone about body x, then the ball about its apex), in place. */
+void orc_sector_project(double* T, double Tmax, double tan_delta);
 
 /* Jacobi eigenvalues of a dense symmetric matrix (in place; returns the largest). */
 double orc_sym_eig_max(int n, double* M);

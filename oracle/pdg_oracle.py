@@ -59,6 +59,7 @@ class Params(C.Structure):
         ("scp_eps_step", C.c_double), ("scp_eps_defect", C.c_double),
         ("rk4_substeps", C.c_int),
         ("tf_guess", C.c_double),
+        ("soc_thrust", C.c_int),
     ]
 
 
@@ -72,7 +73,9 @@ class QP(C.Structure):
                 ("umin", _DP), ("umax", _DP),
                 ("zi", C.c_double * 15), ("zf", C.c_double * 15), ("fixf", C.c_int * 15),
                 ("w_cost", C.c_double), ("w_prox", C.c_double), ("w_ep", C.c_double),
-                ("ecost", C.c_double * 15)]
+                ("ecost", C.c_double * 15),
+                ("soc", C.c_int), ("Tbar", _DP), ("soc_Tmax", C.c_double), ("soc_tan", C.c_double),
+                ("soc_PT", C.c_double)]
 
 
 class PD(C.Structure):
@@ -110,6 +113,7 @@ def lib():
             L.orc_pipg_generic.argtypes = [C.POINTER(QP), C.c_double, C.c_double, C.c_double, C.c_int,
                                            _DP, _DP, _DP, _DP, _DP, _DP]
             L.orc_z_pack.argtypes = [C.POINTER(QP), C.POINTER(PD), _DP]
+            L.orc_sector_project.argtypes = [_DP, C.c_double, C.c_double]
             L.orc_sym_eig_max.argtypes = [C.c_int, _DP]
             L.orc_sym_eig_max.restype = C.c_double
             L.orc_init_guess.argtypes = [P, C.c_int, _DP, _DP, _DP]
@@ -150,6 +154,7 @@ def make_params(p: Dict) -> Params:
             arr[i] = float(p[k][i])
     for i in range(15):
         s.fix_f[i] = int(p["fix_f"][i])
+    s.soc_thrust = int(p.get("soc_thrust", 0))
     return s
 
 
@@ -230,6 +235,9 @@ class QPData:
         self.fixf = np.zeros(NX, np.int32)
         self.ecost = np.zeros(NX)
         self.w_cost = self.w_prox = self.w_ep = 0.0
+        self.Tbar = np.zeros((N, 3))
+        self.soc = 0
+        self.soc_Tmax = self.soc_tan = self.soc_PT = 0.0
 
     def cstruct(self) -> QP:
         q = QP()
@@ -242,6 +250,9 @@ class QPData:
             q.fixf[i] = int(self.fixf[i])
             q.ecost[i] = self.ecost[i]
         q.w_cost, q.w_prox, q.w_ep = self.w_cost, self.w_prox, self.w_ep
+        q.soc = int(self.soc)
+        q.Tbar = _d(self.Tbar)
+        q.soc_Tmax, q.soc_tan, q.soc_PT = self.soc_Tmax, self.soc_tan, self.soc_PT
         return q
 
     def pull(self, q: QP):
@@ -250,6 +261,8 @@ class QPData:
         self.fixf[:] = list(q.fixf)
         self.ecost[:] = list(q.ecost)
         self.w_cost, self.w_prox, self.w_ep = q.w_cost, q.w_prox, q.w_ep
+        self.soc = q.soc
+        self.soc_Tmax, self.soc_tan, self.soc_PT = q.soc_Tmax, q.soc_tan, q.soc_PT
 
 
 class PDState:
@@ -336,6 +349,12 @@ def pipg_generic(qp: QPData, alpha, omega, rho, jmax, z1, eta1, chi1):
                            _d(np.ascontiguousarray(z1, np.float64)), _d(np.ascontiguousarray(eta1, np.float64)),
                            _d(np.ascontiguousarray(chi1, np.float64)), _d(z), _d(w), _d(v))
     return z, w, v
+
+
+def sector_project(T, Tmax, tan_delta):
+    T = np.array(T, dtype=np.float64)
+    lib().orc_sector_project(_d(T), float(Tmax), float(tan_delta))
+    return T
 
 
 def sym_eig_max(M: np.ndarray) -> float:

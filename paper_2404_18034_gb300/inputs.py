@@ -61,6 +61,7 @@ def load_params(path: Optional[str] = None, nu: Optional[int] = None, **override
         p[k] = float(raw[k])
     for k in ("pipg_jmax", "pipg_jcheck", "pow_jmax", "scp_jmax", "rk4_substeps"):
         p[k] = int(raw[k])
+    p["soc_thrust"] = int(raw.get("soc_thrust", 0))
     for k in ("g_I", "J_B", "r_T_B"):
         p[k] = np.asarray(raw[k], dtype=np.float64)
     p["theta_max"] = raw["theta_max_deg"] * d2r
