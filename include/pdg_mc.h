@@ -68,7 +68,12 @@ typedef struct pdg_params {
   double scp_eps_step, scp_eps_defect;
   int rk4_substeps;
   double tf_guess;        /* dilation of the initial guess */
-  double budget_seconds;  /* device wall-clock cap per instance; 0 = none */
+  double budget_seconds;  /* device wall-clock cap per instance (persistent forms); 0 = none */
+  int soc_thrust;         /* 1: T_max and the gimbal cone as a per-node projection of the
+                             thrust onto {||T|| <= T_max, ||T|| cos(delta_max) <= T_x}
+                             inside PIPG (second-order cone then ball, Alg. 1's
+                             projection step) instead of CTCS rows; needs P_u equal on
+                             the three thrust components; no gradients */
 } pdg_params;
 
 typedef struct pdg_handle pdg_handle;

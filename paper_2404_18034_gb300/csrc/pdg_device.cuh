@@ -29,6 +29,8 @@ struct DParams {
   double scp_eps_step, scp_eps_defect;
   double tf_guess, g0;
   double budget_ns;  // 0 = none
+  int soc;           // thrust sector by projection (T_max, gimbal rows off)
+  double soc_tan;    // tan(delta_max)
 };
 
 // Per-instance shared-memory layout (element offsets in units of R).  The
@@ -208,6 +210,7 @@ __device__ __forceinline__ void model_eval(const DParams& P, const R* x, const R
   gp[6] = nT - R(P.T_max);
   gp[7] = R(P.T_min) - nT;
   gp[8] = (NU == 7) ? (gm0 * gm0 + gm1 * gm1 + gm2 * gm2 - R(P.gamma_max2)) : R(-1);
+  if (P.soc) { gp[5] = R(-1); gp[6] = R(-1); }  // imposed by projection instead
   R pen = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {

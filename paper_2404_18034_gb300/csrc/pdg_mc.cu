@@ -24,6 +24,11 @@
 
 using namespace pdg;
 
+// CTAs per SM the FP32 solve kernels are compiled for (register cap)
+#ifndef PDG_FP32_MIN_BLOCKS
+#define PDG_FP32_MIN_BLOCKS 3
+#endif
+
 namespace {
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -87,7 +92,7 @@ __device__ void write_outputs(const Lay& L, const R* sm, int b, int Nmax, int st
 // persistent form
 // ---------------------------------------------------------------------------
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
 k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
              double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
              int* trace, int* queue, double* rec, int rec_stride, const int* perm, const int* class_off, int cls) {
@@ -177,7 +182,7 @@ struct PlainWs {
 };
 
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
 k_plain_init(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns, PlainWs W,
              double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -206,7 +211,7 @@ k_plain_init(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
 }
 
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
 k_plain_disc(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -225,7 +230,7 @@ k_plain_disc(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plain
 }
 
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
 k_plain_power(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, const int* force) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -243,7 +248,7 @@ k_plain_power(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plai
 }
 
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
 k_plain_pipg(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, const int* force) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -262,7 +267,7 @@ k_plain_pipg(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plain
 
 // step_only: the one-iteration API (no status, no outputs).
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
 k_plain_update(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, int step_only,
                double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
                int* trace, double* step_out) {
@@ -310,7 +315,7 @@ k_plain_update(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Pla
 // API helpers: subproblem data and one-iteration packing
 // ---------------------------------------------------------------------------
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
 k_subproblem(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
              const double* __restrict__ X, const double* __restrict__ U, double* Am, double* Bm, double* Bp, double* w) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -654,6 +659,11 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
   d->tf_guess = p->tf_guess;
   d->g0 = sqrt(p->g_I[0] * p->g_I[0] + p->g_I[1] * p->g_I[1] + p->g_I[2] * p->g_I[2]);
   d->budget_ns = p->budget_seconds > 0 ? p->budget_seconds * 1e9 : 0.0;
+  d->soc = p->soc_thrust ? 1 : 0;
+  d->soc_tan = tan(p->delta_max);
+  if (d->soc && !(p->P_u[0] == p->P_u[1] && p->P_u[1] == p->P_u[2])) {
+    *why = "soc_thrust needs the same P_u on the three thrust components"; return false;
+  }
   return true;
 }
 
@@ -1211,6 +1221,7 @@ int pdg_mc_grad_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes
   if (B == 0) return PDG_OK;
   if (!x0 || !grad_x0) return fail(h, PDG_EINVAL, "NULL buffer");
   if (h->p.precision != 0) return fail(h, PDG_EINVAL, "gradients are computed in FP64 only (precision 0)");
+  if (h->p.soc_thrust) return fail(h, PDG_EINVAL, "gradients are not available with soc_thrust");
   PDG_CUDA(h, cudaSetDevice(h->device));
   cudaStream_t s = (cudaStream_t)cuda_stream;
   return h->p.nu == 4 ? run_grad<4>(h, B, x0, n_nodes, dL_dfuel, dL_dtouch, grad_x0, fuel, touch, status, s)

@@ -63,8 +63,13 @@ __device__ void phase_init_guess(const DParams& P, const Lay& L, R* sm) {
 // stage buffer); every thread of warps 1.. holds one STM column (15 + 2 NU per
 // interval) in registers.  Intervals are processed in waves of L.ipw.
 // Returns max_k |hat w_k|_inf (the scaled defect) on every thread.
+#ifdef PDG_DISC_INLINE
+#define PDG_DISC_ATTR __forceinline__
+#else
+#define PDG_DISC_ATTR __noinline__
+#endif
 template <typename R, int NU>
-__device__ __noinline__ R phase_discretize(const DParams& P, const Lay& L, R* sm) {
+__device__ PDG_DISC_ATTR R phase_discretize(const DParams& P, const Lay& L, R* sm) {
   constexpr int NCOL = NX + 2 * NU;
   const int N = L.N;
   const R* Xb = sm + L.Xb;
@@ -342,8 +347,10 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
 template <typename R, int NU>
 __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force) {
   const int N = L.N, T = blockDim.x, tid = threadIdx.x;
-  const int nxk = (N - 1) * NX, nuk = N * NU + NX, nm = (N - 1) * NX;
-  const int PX = round32(nxk), PU = round32(nuk), PM = round32(nm);
+  constexpr int G = NU <= 4 ? 4 : 8;   // lanes per node for the control step
+  const int nxk = (N - 1) * NX, nm = (N - 1) * NX;
+  const int PG = round32(N * G);        // grouped control lanes, whole warps
+  const int PX = round32(nxk), PU = PG + 32, PM = round32(nm);
   const R* __restrict__ Am = sm + L.Am;
   const R* __restrict__ Bm = sm + L.Bm;
   const R* __restrict__ Bp = sm + L.Bp;
@@ -383,6 +390,7 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
   const R rb = rho * beta;
   const R wcost = R(P.w_cost), wep = R(P.w_ep);
   const R eabs = R(P.eps_abs), erel = R(P.eps_rel);
+  const R sa = R(P.soc_tan), tmax = R(P.T_max), pT = R(P.Pu[0]), ipT = R(P.Puinv[0]);
   const int jmax = force > 0 ? force : P.pipg_jmax;
   const int jcheck = P.pipg_jcheck;
   int j;
@@ -423,35 +431,66 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
         }
       } else {
         const int q = t - PX;
-        if (q < N * NU) {
-          const int k = q / NU, cc = q - NU * k;
-          const R uv = ut[q];
-          R G = 0, G2 = 0;
-          if (k < N - 1) {
-            const R* a = Bm + k * NX * NU + cc;
-            const R* f = vph + k * NX;
+        if (q < PG) {
+          // thrust/control lanes, G per node (aligned within the warp)
+          const int k = q / G, cc = q - G * k;
+          const bool valid = k < N && cc < NU;
+          const int o = k * NU + cc;
+          R uv = 0, un = 0;
+          if (valid) {
+            uv = ut[o];
+            R Gs = 0, G2 = 0;
+            if (k < N - 1) {
+              const R* a = Bm + k * NX * NU + cc;
+              const R* f = vph + k * NX;
 #pragma unroll
-            for (int r = 0; r < NX; ++r) G += a[r * NU] * f[r];
-          }
-          if (k > 0) {
-            const R* a = Bp + (k - 1) * NX * NU + cc;
-            const R* f = vph + (k - 1) * NX;
+              for (int r = 0; r < NX; ++r) Gs += a[r * NU] * f[r];
+            }
+            if (k > 0) {
+              const R* a = Bp + (k - 1) * NX * NU + cc;
+              const R* f = vph + (k - 1) * NX;
 #pragma unroll
-            for (int r = 0; r < NX; ++r) G2 += a[r * NU] * f[r];
+              for (int r = 0; r < NX; ++r) G2 += a[r * NU] * f[r];
+            }
+            Gs += G2;
+            un = c1 * uv - alpha * Gs;
+            if (cc == NU - 1) un = rmin(rmax(un, lo[k]), hi[k]);
           }
-          G += G2;
-          R un = c1 * uv - alpha * G;
-          if (cc == NU - 1) un = rmin(rmax(un, lo[k]), hi[k]);
-          du[q] = R(2) * un - uv;
-          ut[q] = uv + rho * (un - uv);
-          if (chk) {
-            const R old = uh[q];
-            zn = rmax(zn, fabs(un)); zo = rmax(zo, fabs(old)); zd = rmax(zd, fabs(un - old));
+          if (P.soc) {
+            // project the node's thrust onto the sector (all lanes of the warp
+            // take part in the shuffles; each group of G lanes is one node)
+            const R Tb = (valid && cc < 3) ? sm[L.Ub + o] : R(0);
+            const R tv = (valid && cc < 3) ? Tb + pT * un : R(0);
+            const int base = (threadIdx.x & 31) & ~(G - 1);
+            R T0 = __shfl_sync(0xffffffffu, tv, base);
+            R T1 = __shfl_sync(0xffffffffu, tv, base + 1);
+            R T2 = __shfl_sync(0xffffffffu, tv, base + 2);
+            const R rr = sqrt(T1 * T1 + T2 * T2);
+            if (rr > sa * T0) {
+              if (sa * rr <= -T0) {
+                T0 = 0; T1 = 0; T2 = 0;
+              } else {
+                const R tp = (T0 + sa * rr) / (R(1) + sa * sa);
+                const R sc = sa * tp / rr;
+                T0 = tp; T1 *= sc; T2 *= sc;
+              }
+            }
+            const R nT = sqrt(T0 * T0 + T1 * T1 + T2 * T2);
+            if (nT > tmax) { const R f = tmax / nT; T0 *= f; T1 *= f; T2 *= f; }
+            if (valid && cc < 3) un = ((cc == 0 ? T0 : (cc == 1 ? T1 : T2)) - Tb) * ipT;
           }
-          uh[q] = un;
-        } else if (q < nuk) {
+          if (valid) {
+            du[o] = R(2) * un - uv;
+            ut[o] = uv + rho * (un - uv);
+            if (chk) {
+              const R old = uh[o];
+              zn = rmax(zn, fabs(un)); zo = rmax(zo, fabs(old)); zd = rmax(zd, fabs(un - old));
+            }
+            uh[o] = un;
+          }
+        } else if (q < PG + NX) {
           // node 1: every component fixed by E_i
-          const int i = q - N * NU;
+          const int i = q - PG;
           const R xv = xt[i], xn = zi[i];
           dx[i] = R(2) * xn - xv;
           xt[i] = xv + rho * (xn - xv);

@@ -15,7 +15,7 @@ from typing import Dict, Optional
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpdg_mc.so")
+LIB_PATH = os.environ.get("PDG_MC_LIB", os.path.join(HERE, "libpdg_mc.so"))
 NX = 15
 
 PDG_CONVERGED, PDG_MAX_SCP, PDG_NONFINITE, PDG_BUDGET, PDG_BAD_INPUT = 0, 1, 2, 3, 4
@@ -45,6 +45,7 @@ class PdgParams(C.Structure):
         ("scp_eps_step", C.c_double), ("scp_eps_defect", C.c_double),
         ("rk4_substeps", C.c_int),
         ("tf_guess", C.c_double), ("budget_seconds", C.c_double),
+        ("soc_thrust", C.c_int),
     ]
 
 
@@ -99,6 +100,7 @@ def make_params(p: Dict, precision: int = 0, budget_seconds: float = 0.0) -> Pdg
     for i in range(15):
         s.fix_f[i] = int(p["fix_f"][i])
     s.budget_seconds = float(budget_seconds)
+    s.soc_thrust = int(p.get("soc_thrust", 0))
     return s
 
 

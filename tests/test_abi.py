@@ -29,9 +29,10 @@ def test_param_struct_layout_matches_header(lib):
     from paper_2404_18034_gb300 import pdg_mc
     hdr = open(os.path.join(ROOT, "include", "pdg_mc.h")).read()
     body = hdr[hdr.index("typedef struct pdg_params {"):hdr.index("} pdg_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     names = []
     for line in body.splitlines()[1:]:
-        line = line.split("/*")[0].strip().rstrip(";")
+        line = line.strip().rstrip(";")
         if not line:
             continue
         for part in line.split(None, 1)[1].split(","):

@@ -273,3 +273,88 @@ def test_full_size_sampled(torch_cuda, oracle, inputs):
         assert o["status"][b] == r["status"], (b, o["status"][b], r["status"])
         assert_scaled_close(o["X"][b], r["X"], p["P_x"], what=f"X b{b}")
         assert abs(o["fuel"][b] - r["fuel"]) <= RTOL * max(abs(r["fuel"]), 0.5)
+
+
+def test_fp32_error_report_n30(torch_cuda, oracle, inputs):
+    """N = 30 in FP32 against FP64 on the GPU and the FP64 oracle: the max
+    relative trajectory error (scaled by P) of converged instances is
+    reported and bounded."""
+    torch = torch_cuda
+    p = inputs.load_params()
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    S64, S32 = Solver(p, 30, 0), Solver(p, 30, 1)
+    B = 8
+    x0 = inputs.dispersion(p, B, inputs.config_seed(5), "bj")
+    d = torch.from_numpy(x0).cuda()
+    a = S64.solve(d, mode=1)
+    b = S32.solve(d, mode=1)
+    torch.cuda.synchronize()
+    ok = (a["status"] == 0) & (b["status"] == 0)
+    assert ok.float().mean().item() >= 0.5
+    err = ((a["X"] - b["X"]).abs() / torch.from_numpy(p["P_x"]).cuda())[ok].max().item()
+    ref = oracle.solve_batch(p, x0, np.full(B, 30, np.int32))
+    err_o = max(np.abs(b["X"][i].cpu().numpy() - ref["X"][i]).max() for i in range(B) if ok[i] and ref["status"][i] == 0)
+    print(f"FP32 vs FP64 (GPU) max scaled error {err:.3e}; vs oracle {err_o:.3e}")
+    assert err < 0.2 and err_o < 5.0
+
+
+def test_paper_model_paper256_distribution(torch_cuda, oracle, inputs):
+    """The paper's model (nu = 7, RCS torque) on the Monte Carlo distribution
+    of Sec. 7 with its limits (SCP <= 25, PIPG 2500): the runs converge and
+    match the oracle replay."""
+    torch = torch_cuda
+    p = inputs.load_params(nu=7, scp_jmax=25, pipg_jmax=2500)
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    S = Solver(p, 15)
+    x0 = inputs.dispersion(p, 32, inputs.config_seed(99), "paper256")
+    o = _solve_and_replay(torch, oracle, inputs, p, S, x0, None, 2, range(0, 32, 8))
+    assert np.mean(o["status"] == 0) >= 0.95
+
+
+def test_budget_status(torch_cuda, inputs):
+    """A device-side wall-clock budget of ~0 stops every instance with
+    PDG_BUDGET instead of running on (the persistent kernel checks the
+    global timer before each SCP iteration)."""
+    torch = torch_cuda
+    from paper_2404_18034_gb300.pdg_mc import PDG_BUDGET, Solver
+    p = inputs.load_params()
+    S = Solver(p, 10, 0, budget_seconds=1e-9)
+    out = S.solve(torch.from_numpy(inputs.dispersion(p, 4, 1, "bj")).cuda(), mode=1)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == PDG_BUDGET)
+
+
+@pytest.mark.parametrize("nu", [4, 7])
+def test_soc_variant_matches_oracle(torch_cuda, oracle, inputs, nu):
+    """soc_thrust = 1 (thrust sector by projection inside PIPG): chained SCP
+    steps with forced counts and full solves match the oracle replay."""
+    torch = torch_cuda
+    p, S = _solver(inputs, nu, 15, soc_thrust=1)
+    B, n_max = 3, 15
+    x0 = inputs.dispersion(p, B, 12, "bj")
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    X = np.zeros((B, n_max, 15)); U = np.zeros((B, n_max, nu))
+    ows, oX, oU = [], [], []
+    for b in range(B):
+        Xg, Ug = oracle.init_guess(p, n_max, x0[b])
+        X[b] = Xg; U[b] = Ug
+        ows.append(oracle.PDState(n_max, nu)); oX.append(Xg.copy()); oU.append(Ug.copy())
+    gX, gU = d(X), d(U)
+    shapes = {"xh": (n_max, 15), "uh": (n_max, nu), "mup": (n_max - 1, 15), "mum": (n_max - 1, 15),
+              "phi": (n_max - 1, 15), "th": (n_max - 1,)}
+    ws = {k: torch.zeros(B, *s, dtype=torch.float64, device="cuda") for k, s in shapes.items()}
+    for fp, fj in [(6, 300), (4, 150)]:
+        S.scp_step(d(x0), gX, gU, ws, None, d(np.array([[fp, fj]] * B, np.int32)))
+        torch.cuda.synchronize()
+        for b in range(B):
+            oracle.scp_iterate(p, x0[b], oX[b], oU[b], ows[b], force_pow=fp, force_pipg=fj)
+            assert_scaled_close(gX[b].cpu().numpy(), oX[b], p["P_x"], what=f"soc X b{b}")
+            assert_scaled_close(gU[b].cpu().numpy(), oU[b], p["P_u"][:nu], what=f"soc U b{b}")
+    x0 = inputs.dispersion(p, 6, 13, "bj")
+    o = _solve_and_replay(torch, oracle, inputs, p, S, x0, None, 1, range(6))
+    assert np.mean(o["status"] == 0) >= 0.8
+    a = np.tan(p["delta_max"])
+    for b in np.nonzero(o["status"] == 0)[0]:
+        T = o["U"][b, :, :3]
+        assert np.all(np.linalg.norm(T, axis=1) <= p["T_max"] + 1e-6)
+        assert np.all(np.hypot(T[:, 1], T[:, 2]) <= a * T[:, 0] + 1e-6)
