@@ -66,6 +66,12 @@ def parse():
     ap.add_argument("--nu", type=int, default=4, choices=[4, 7], help="7: the paper's model with the RCS torque")
     ap.add_argument("--uneven", action="store_true", help="N per instance uniform in {10, 15, 20, 30}")
     ap.add_argument("--grad", action="store_true", help="time gradients (pdg_mc_grad_batch) instead of solves")
+    ap.add_argument("--soc", action="store_true",
+                    help="thrust magnitude and gimbal bounds as a second-order-cone projection in PIPG")
+    ap.add_argument("--pipg-form", type=int, default=0, choices=[0, 1, 2],
+                    help="PIPG layout: 0 autotune cache / automatic, 1 shared memory, 2 registers")
+    ap.add_argument("--err-sample", type=int, default=512,
+                    help="fp32: instances re-solved in fp64 on the GPU to report the fp32 error (0: off)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -91,7 +97,8 @@ def reduce_over_ranks(total_ms: float, converged: int, solved: int, dist, device
 def workload_name(a):
     n = "Nuneven10-30" if a.uneven else f"N{a.nodes}"
     nu = "" if a.nu == 4 else f"_nu{a.nu}"
-    return f"pdg6dof_{a.dispersion}_B{a.batch}_{n}{nu}_{a.precision}_{a.mode}"
+    soc = "_soc" if getattr(a, "soc", False) else ""
+    return f"pdg6dof_{a.dispersion}_B{a.batch}_{n}{nu}{soc}_{a.precision}_{a.mode}"
 
 
 class ClockSampler:
@@ -246,6 +253,37 @@ def run_grad(a):
     S.close()
 
 
+def fp32_error(p, a, S32, x0, Ns, out32, mode, dev):
+    """Re-solve the first instances in FP64 on the GPU and report the FP32 path's
+    largest deviation on instances that converged in both: trajectories scaled
+    per component by max(|x64|, P), final time and fuel relative."""
+    import torch
+
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    n = min(a.err_sample, a.batch)
+    S64 = Solver(p, a.nodes, 0, mode=mode)
+    o64 = S64.solve(x0[:n].contiguous(), None if Ns is None else Ns[:n].contiguous(), mode=mode)
+    torch.cuda.synchronize(dev)
+    ok = ((o64["status"] == 0) & (out32["status"][:n] == 0)).cpu().numpy()
+    Px = np.asarray(p["P_x"])
+    Pu = np.asarray(p["P_u"])[:p["nu"]]
+    X32, X64 = out32["X"][:n].cpu().numpy()[ok], o64["X"].cpu().numpy()[ok]
+    U32, U64 = out32["U"][:n].cpu().numpy()[ok], o64["U"].cpu().numpy()[ok]
+    ex = np.abs(X32 - X64) / np.maximum(np.abs(X64), Px)
+    eu = np.abs(U32 - U64) / np.maximum(np.abs(U64), Pu)
+    if Ns is not None:  # nodes past an instance's N are padding
+        nn = Ns[:n].cpu().numpy()[ok]
+        live = np.arange(X32.shape[1])[None, :] < nn[:, None]
+        ex, eu = ex[live], eu[live]
+    rel = lambda k: float(np.max(np.abs(out32[k][:n].cpu().numpy()[ok] - o64[k].cpu().numpy()[ok])
+                                 / np.abs(o64[k].cpu().numpy()[ok]))) if ok.any() else None
+    S64.close()
+    return {"instances": int(ok.sum()), "of": n, "max_scaled_err_X": float(ex.max()) if ok.any() else None,
+            "max_scaled_err_U": float(eu.max()) if ok.any() else None, "max_rel_err_tf": rel("tf"),
+            "max_rel_err_fuel": rel("fuel"),
+            "note": "first instances of the batch re-solved by the FP64 kernel; both converged"}
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -265,7 +303,7 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     prec = 0 if a.precision == "fp64" else 1
-    p = inputs.load_params(nu=a.nu)
+    p = inputs.load_params(nu=a.nu, soc_thrust=int(a.soc))
     seed = shard_seed(inputs.config_seed(2), rank)
     x0h = inputs.dispersion(p, a.batch, seed, a.dispersion)
     x0 = torch.from_numpy(x0h).to(dev)
@@ -276,6 +314,11 @@ def run_ours(a):
     mode = {"plain": 0, "persistent": 1, "classed": 2}[a.mode]
     from paper_2404_18034_gb300.autotune import DEFAULT_CACHE
     S = Solver(p, a.nodes, prec, tune_cache=DEFAULT_CACHE, mode=mode)
+    if a.pipg_form:
+        S.set_pipg_form(a.pipg_form)
+        if S.tuned_form != a.pipg_form:  # cached threads were tuned for the other layout
+            S.set_threads(0)
+            S.tuned_threads = None
     out = S.alloc_outputs(a.batch, dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
@@ -349,6 +392,10 @@ def run_ours(a):
         e2e = {"value": e2e_conv_all / (e2e_ms_max * 1e-3), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    err = None
+    if prec == 1 and a.err_sample > 0 and rank == 0:
+        err = fp32_error(p, a, S, x0, Ns, out, mode, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline(p, a, inputs.config_seed(2), a.cpu_sample)
@@ -365,6 +412,7 @@ def run_ours(a):
                        "dispersion": a.dispersion, "parallelism": f"dp{world}",
                        "l2": "256 MiB buffer written between timed steps",
                        "threads_per_cta": info["threads"], "ctas_per_sm": info["ctas_per_sm"],
+                       "pipg_form": {1: "shared-memory blocks", 2: "register-resident blocks"}.get(info["pipg_form"]),
                        "threads_from_autotune_cache": S.tuned_threads is not None,
                        "smem_bytes_per_cta": info["smem_bytes"]},
             "converged_fraction": conv / a.batch,
@@ -384,6 +432,8 @@ def run_ours(a):
                          "frac_of_probe": (achieved / probe) if probe else None},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": launches,
         }
+        if err is not None:
+            line["fp32_vs_fp64"] = err
         print(json.dumps(line), flush=True)
     S.close()
     if world > 1:

@@ -173,9 +173,29 @@ int pdg_mc_grad_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes
  * Synchronous; no device work. */
 int pdg_mc_launch_info(pdg_handle* h, int* threads, int* ctas_per_sm, int* smem_bytes);
 
-/* Override the threads-per-CTA of the solve kernels (multiple of 32, 0 =
- * automatic).  Used by the autotuner. */
+/* Override the threads-per-CTA of the solve kernels (multiple of 32 up to
+ * 640, 0 = automatic).  Used by the autotuner.  The shared-memory PIPG form
+ * runs at most 512; the register form needs at least one thread per dual row
+ * plus the control lanes (see pdg_mc_set_pipg_form); a solve whose setting
+ * does not fit returns PDG_EINVAL. */
 int pdg_mc_set_threads(pdg_handle* h, int threads);
+
+/* Choose how the PIPG loop (Alg. PIPG_custom, Sec. 4.3) is laid out on the
+ * CTA.  Results agree to rounding; only speed differs.
+ *   form 1: blocks hat A^-, hat B^+- and the iterates in shared memory, any
+ *           thread count (one thread per block row or column, looped);
+ *   form 2: every thread keeps its block rows/columns and iterate entries in
+ *           registers for the whole loop; only the vectors exchanged between
+ *           the primal and dual steps go through shared memory.  Needs
+ *           round32(15 (N-1)) + round32(N G) threads, G = 4 (nu = 4) or 8,
+ *           at most 640 (FP32) or 512 (FP64);
+ *   form 0: automatic (default) -- form 2 for FP32 when it fits, else form 1.
+ * Returns PDG_EINVAL for another value.  Synchronous; no device work. */
+int pdg_mc_set_pipg_form(pdg_handle* h, int form);
+
+/* The PIPG form (1 or 2) of the handle's last solve or SCP step, 0 before
+ * the first; PDG_EINVAL for a NULL handle. */
+int pdg_mc_pipg_form(const pdg_handle* h);
 
 /* Solve without allocating: for callers that cannot call cudaMalloc while
  * they run, e.g. code inside a region that a memory pool or allocator owns,

@@ -1,11 +1,13 @@
 """Autotuner for the launch shape of the batched solver.
 
-For one (device, n_max, nu, precision, form) it times a solve of a seeded
-batch at every candidate CTA size (multiples of 32 that leave room for at
-least one discretization interval and fit in shared memory), keeps the
-fastest by converged solves per second, and records it in a JSON cache keyed
-by "device|n_max|nu|precision|mode".  Solver(tune_cache=...) applies a cached
-choice through pdg_mc_set_threads.
+For one (device, n_max, nu, precision, execution form) it times a solve of a
+seeded batch at every candidate (PIPG layout, CTA size) pair -- the
+shared-memory PIPG form at multiples of 32 that leave room for at least one
+discretization interval and fit in shared memory, the register form from the
+threads it needs up to its limit -- keeps the fastest by converged solves per
+second, and records it in a JSON cache keyed by
+"device|n_max|nu|precision|mode".  Solver(tune_cache=...) applies a cached
+choice through pdg_mc_set_pipg_form and pdg_mc_set_threads.
 
   python -m paper_2404_18034_gb300.autotune --nodes 15 --precision fp64 --batch 2048
 """
@@ -15,7 +17,7 @@ import argparse
 import json
 import os
 import time
-from typing import Dict, Iterable, Optional
+from typing import Dict, Iterable, Optional, Tuple
 
 import numpy as np
 
@@ -36,17 +38,41 @@ def load_cache(path: str = DEFAULT_CACHE) -> Dict:
     return {}
 
 
-def lookup(device_name: str, n_max: int, nu: int, precision: int, mode: int, path: str = DEFAULT_CACHE) -> Optional[int]:
+def lookup(device_name: str, n_max: int, nu: int, precision: int, mode: int,
+           path: str = DEFAULT_CACHE) -> Optional[Tuple[int, int]]:
+    """(threads, PIPG form) of a cached choice, or None.  Entries written
+    before the register form existed carry no form: they are form 1."""
     e = load_cache(path).get(cache_key(device_name, n_max, nu, precision, mode))
-    return int(e["threads"]) if e else None
+    return (int(e["threads"]), int(e.get("form", 1))) if e else None
 
 
-def candidates(n_max: int, nu: int, precision: int) -> Iterable[int]:
-    """CTA sizes with at least one discretization interval per wave whose
-    shared-memory image fits on an SM (mirrors the kernel's layout rule)."""
+def round32(x: int) -> int:
+    return (x + 31) // 32 * 32
+
+
+def reg_threads(n_max: int, nu: int) -> int:
+    """Threads the register PIPG form needs (one per dual row, whole warps,
+    plus 4 or 8 lanes per node for the controls)."""
+    return round32((n_max - 1) * NX) + round32(n_max * (4 if nu <= 4 else 8))
+
+
+def candidates(n_max: int, nu: int, precision: int, forms: Iterable[int] = (1, 2)) -> Iterable[Tuple[int, int]]:
+    """(form, CTA size) pairs with at least one discretization interval per
+    wave whose shared-memory image fits on an SM (mirrors the kernel's layout
+    rule); the register form from its minimum up to 640 (FP32) or 512 threads."""
+    out = []
+    if 1 in forms:
+        out += [(1, t) for t in _fitting(range(128, 513, 32), n_max, nu, precision)]
+    if 2 in forms:
+        hi = 640 if precision == 1 else 512
+        out += [(2, t) for t in _fitting(range(reg_threads(n_max, nu), hi + 1, 32), n_max, nu, precision)]
+    return out
+
+
+def _fitting(ts: Iterable[int], n_max: int, nu: int, precision: int) -> Iterable[int]:
     ncol = NX + 2 * nu
     esz = 8 if precision == 0 else 4
-    for t in range(128, 513, 32):
+    for t in ts:
         ipw = min(32, (t - 32) // ncol)
         if ipw < 1:
             continue
@@ -60,7 +86,8 @@ def candidates(n_max: int, nu: int, precision: int) -> Iterable[int]:
 
 
 def autotune(params: Dict, n_max: int, precision: int = 0, mode: int = 1, batch: int = 2048, seed: int = 7,
-             reps: int = 2, path: str = DEFAULT_CACHE, cands: Optional[Iterable[int]] = None) -> Dict:
+             reps: int = 2, path: str = DEFAULT_CACHE, cands: Optional[Iterable[Tuple[int, int]]] = None,
+             forms: Iterable[int] = (1, 2)) -> Dict:
     import torch
 
     from . import inputs
@@ -70,7 +97,8 @@ def autotune(params: Dict, n_max: int, precision: int = 0, mode: int = 1, batch:
     x0 = torch.from_numpy(inputs.dispersion(params, batch, seed, "bj")).to(dev)
     S = Solver(params, n_max, precision)
     results = {}
-    for t in (cands or candidates(n_max, int(params["nu"]), precision)):
+    for form, t in (cands or candidates(n_max, int(params["nu"]), precision, forms)):
+        S.set_pipg_form(form)
         S.set_threads(t)
         try:
             S.solve(x0, mode=mode)
@@ -86,11 +114,11 @@ def autotune(params: Dict, n_max: int, precision: int = 0, mode: int = 1, batch:
             conv = int((out["status"] == 0).sum().item())
             rate = conv / dt
             best = rate if best is None else max(best, rate)
-        results[t] = best
+        results[(form, t)] = best
     S.close()
-    t_best = max(results, key=results.get)
-    entry = {"threads": int(t_best), "solves_per_s": results[t_best], "batch": batch,
-             "swept": {str(k): v for k, v in sorted(results.items())}}
+    f_best, t_best = max(results, key=results.get)
+    entry = {"threads": int(t_best), "form": int(f_best), "solves_per_s": results[(f_best, t_best)], "batch": batch,
+             "swept": {f"form{f}:{k}": v for (f, k), v in sorted(results.items())}}
     cache = load_cache(path)
     cache[cache_key(name, n_max, int(params["nu"]), precision, mode)] = entry
     with open(path, "w") as fh:
@@ -107,12 +135,14 @@ def main():
     ap.add_argument("--batch", type=int, default=2048)
     ap.add_argument("--nu", type=int, default=4)
     ap.add_argument("--cache", default=DEFAULT_CACHE)
+    ap.add_argument("--forms", type=int, nargs="+", default=[1, 2], choices=[1, 2])
     a = ap.parse_args()
     p = inputs.load_params(nu=a.nu)
     for n in a.nodes:
         for pr in a.precision:
             for m in a.mode:
-                e = autotune(p, n, 0 if pr == "fp64" else 1, 1 if m == "persistent" else 0, a.batch, path=a.cache)
+                e = autotune(p, n, 0 if pr == "fp64" else 1, 1 if m == "persistent" else 0, a.batch, path=a.cache,
+                             forms=a.forms)
                 print(json.dumps({"nodes": n, "precision": pr, "mode": m, **e}))
 
 

@@ -29,7 +29,22 @@ using namespace pdg;
 #define PDG_FP32_MIN_BLOCKS 3
 #endif
 
+// PIPG forms: 1 = blocks in shared memory (phase_pipg), 2 = blocks and
+// iterates in registers (phase_pipg_reg).  The register form runs one thread
+// per dual row plus the control lanes, so its kernels are built for up to
+// PDG_REG_MAXT threads (FP32) or 512 (FP64).
+#define PDG_REG_MAXT_F32 544
+#define PDG_LB(R, PV)                                                                       \
+  __launch_bounds__((PV) == 2 && sizeof(R) == 4 ? PDG_REG_MAXT_F32 : 512,                   \
+                    sizeof(R) == 4 && (PV) != 2 ? PDG_FP32_MIN_BLOCKS : 1)
+
 namespace {
+
+template <typename R, int NU, int PV>
+__device__ __forceinline__ int run_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force) {
+  if constexpr (PV == 2) return phase_pipg_reg<R, NU>(P, L, sm, sigma, force);
+  else return phase_pipg<R, NU>(P, L, sm, sigma, force);
+}
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -91,14 +106,24 @@ __device__ void write_outputs(const Lay& L, const R* sm, int b, int Nmax, int st
 // ---------------------------------------------------------------------------
 // persistent form
 // ---------------------------------------------------------------------------
-template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
+template <typename R, int NU, int PV>
+__global__ void PDG_LB(R, PV)
 k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
              double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
              int* trace, int* queue, double* rec, int rec_stride, const int* perm, const int* class_off, int cls) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
   __shared__ int inst;
+  // Per-instance layout and scalars live in shared memory and are re-read
+  // after the phases (which end in barriers), so that no register is held
+  // across the PIPG loop: it gets the whole register budget.
+  __shared__ Lay Ls;
+  __shared__ struct {
+    unsigned long long t_start;
+    long long ptot;
+    double defect, sigma;
+    int b, pit;
+  } C;
   // shape-class launch: this grid serves the instances perm[class_off[cls] ..
   // class_off[cls + 1]) (all of one node count)
   const int nq = perm ? class_off[cls + 1] - class_off[cls] : B;
@@ -116,53 +141,74 @@ k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
       __syncthreads();
       continue;
     }
-    const Lay L = make_lay(N, NU, blockDim.x);
+    // the layout lives in shared memory: read field by field after each
+    // barrier instead of occupying registers across the phases
+    if (threadIdx.x == 0) Ls = make_lay(N, NU, blockDim.x);
+    __syncthreads();
+    const Lay& L = Ls;
     if (!load_x0<R>(L, sm, x0, b)) {
       write_outputs<R, NU>(L, sm, b, Nmax, PDG_BAD_INPUT, 0, 0, X, U, tf, fuel, status, scp_iters, pipg_iters);
       __syncthreads();
       continue;
     }
-    const unsigned long long t_start = globaltimer_ns();
+    if (threadIdx.x == 0) { C.b = b; C.t_start = globaltimer_ns(); C.ptot = 0; }
     phase_init_guess<R, NU>(P, L, sm);
     for (int t = threadIdx.x; t < L.img - L.xh; t += blockDim.x) sm[L.xh + t] = R(0);
     __syncthreads();
     int stat = PDG_MAX_SCP, j;
-    long long ptot = 0;
     for (j = 1; j <= P.scp_jmax; ++j) {
-      if (P.budget_ns > 0.0 && double(globaltimer_ns() - t_start) > P.budget_ns) { stat = PDG_BUDGET; --j; break; }
-      double* rc = rec ? rec + (size_t)b * rec_stride : nullptr;
-      const int ow = N * (NX + NU), nw = L.img - L.xh;
-      if (rc) {  // reference and warm start of this SCP iteration (the last one is kept)
-        for (int t = threadIdx.x; t < N * NX; t += blockDim.x) rc[t] = double(sm[L.Xb + t]);
-        for (int t = threadIdx.x; t < N * NU; t += blockDim.x) rc[N * NX + t] = double(sm[L.Ub + t]);
+      if (P.budget_ns > 0.0 && double(globaltimer_ns() - C.t_start) > P.budget_ns) { stat = PDG_BUDGET; --j; break; }
+      if (rec) {  // reference and warm start of this SCP iteration (the last one is kept)
+        double* rc = rec + (size_t)C.b * rec_stride;
+        const int n = L.N, ow = n * (NX + NU), nw = L.img - L.xh;
+        for (int t = threadIdx.x; t < n * NX; t += blockDim.x) rc[t] = double(sm[L.Xb + t]);
+        for (int t = threadIdx.x; t < n * NU; t += blockDim.x) rc[n * NX + t] = double(sm[L.Ub + t]);
         for (int t = threadIdx.x; t < nw; t += blockDim.x) rc[ow + t] = double(sm[L.xh + t]);
       }
-      const R defect = phase_discretize<R, NU>(P, L, sm);
+      {
+        const R defect = phase_discretize<R, NU>(P, L, sm);
+        if (threadIdx.x == 0) C.defect = double(defect);
+      }
       phase_scale_extra<R, NU>(P, L, sm);
       __syncthreads();
-      int pit;
-      const R sigma = phase_power<R, NU>(P, L, sm, 0, &pit);
-      const int jit = phase_pipg<R, NU>(P, L, sm, sigma, 0);
-      if (rc && threadIdx.x == 0) { rc[ow + nw] = double(sigma); rc[ow + nw + 1] = double(jit); }
+      int jit;
+      {
+        int pit;
+        const R sigma = phase_power<R, NU>(P, L, sm, 0, &pit);
+        if (threadIdx.x == 0) { C.sigma = double(sigma); C.pit = pit; }
+        jit = run_pipg<R, NU, PV>(P, L, sm, sigma, 0);
+      }
+      const int bb = C.b;
+      if (rec && threadIdx.x == 0) {
+        const int ow = L.N * (NX + NU), nw = L.img - L.xh;
+        double* rc = rec + (size_t)bb * rec_stride;
+        rc[ow + nw] = C.sigma;
+        rc[ow + nw + 1] = double(jit);
+      }
       bool bad;
       const R step = phase_update<R, NU>(P, L, sm, &bad);
-      ptot += jit;
-      if (trace && threadIdx.x == 0) {
-        trace[((size_t)b * P.scp_jmax + (j - 1)) * 2 + 0] = pit;
-        trace[((size_t)b * P.scp_jmax + (j - 1)) * 2 + 1] = jit;
+      if (threadIdx.x == 0) {
+        C.ptot += jit;
+        if (trace) {
+          trace[((size_t)bb * P.scp_jmax + (j - 1)) * 2 + 0] = C.pit;
+          trace[((size_t)bb * P.scp_jmax + (j - 1)) * 2 + 1] = jit;
+        }
       }
       if (bad) { stat = PDG_NONFINITE; break; }
-      const R dy = sm[L.Xb + (N - 1) * NX + IY] - sm[L.Xb + IY];
-      if (step <= R(P.scp_eps_step) && defect <= R(P.scp_eps_defect) && dy <= R(N - 1) * R(P.eps_ctcs)) {
+      const int n = L.N;
+      const R dy = sm[L.Xb + (n - 1) * NX + IY] - sm[L.Xb + IY];
+      if (step <= R(P.scp_eps_step) && R(C.defect) <= R(P.scp_eps_defect) && dy <= R(n - 1) * R(P.eps_ctcs)) {
         stat = PDG_CONVERGED;
         break;
       }
     }
     if (j > P.scp_jmax) j = P.scp_jmax;
+    __syncthreads();  // C.ptot written by thread 0 above
+    const int bb = C.b;
     if (trace) {
-      for (int t = threadIdx.x + 2 * j; t < 2 * P.scp_jmax; t += blockDim.x) trace[(size_t)b * P.scp_jmax * 2 + t] = 0;
+      for (int t = threadIdx.x + 2 * j; t < 2 * P.scp_jmax; t += blockDim.x) trace[(size_t)bb * P.scp_jmax * 2 + t] = 0;
     }
-    write_outputs<R, NU>(L, sm, b, Nmax, stat, j, ptot, X, U, tf, fuel, status, scp_iters, pipg_iters);
+    write_outputs<R, NU>(L, sm, bb, Nmax, stat, j, C.ptot, X, U, tf, fuel, status, scp_iters, pipg_iters);
     __syncthreads();
   }
 }
@@ -247,8 +293,8 @@ k_plain_power(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plai
   if (threadIdx.x == 0) { img[L.sc + 0] = sigma; W.pow_it[b] = it; }
 }
 
-template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
+template <typename R, int NU, int PV>
+__global__ void PDG_LB(R, PV)
 k_plain_pipg(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, const int* force) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -260,7 +306,7 @@ k_plain_pipg(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plain
   copy_g2s(sm + L.Am, img + L.Am, L.img - L.Am);     // subproblem + warm start
   __syncthreads();
   const R sigma = img[L.sc + 0];
-  const int it = phase_pipg<R, NU>(P, L, sm, sigma, force ? force[2 * b + 1] : 0);
+  const int it = run_pipg<R, NU, PV>(P, L, sm, sigma, force ? force[2 * b + 1] : 0);
   copy_s2g(img + L.xh, sm + L.xh, L.img - L.xh);
   if (threadIdx.x == 0) W.pipg_it[b] = it;
 }
@@ -552,6 +598,7 @@ struct pdg_handle {
   DParams dp;
   int n_max;
   int threads_override;
+  int pipg_variant = 0;        // 0 auto, 1 shared-memory PIPG, 2 register PIPG
   int device;
   int num_sms;
   std::string err;
@@ -578,7 +625,7 @@ struct pdg_handle {
   void* stage = nullptr;
   size_t stage_bytes = 0;
   // last launch
-  int last_threads = 0, last_ctas = 0, last_smem = 0;
+  int last_threads = 0, last_ctas = 0, last_smem = 0, last_variant = 0;
 };
 
 static std::string g_init_err;
@@ -683,16 +730,58 @@ static int threads_for(int N, int nu, int precision) {
   return t;
 }
 
-static int pick_threads(const pdg_handle* h) {
-  if (h->threads_override > 0) return h->threads_override;
-  return threads_for(h->n_max, h->p.nu, h->p.precision);
+// PIPG form and CTA size for instances of up to N nodes.  Auto (variant 0):
+// FP32 takes the register form when its threads fit (its shared-memory form
+// is bound by shared-memory bandwidth), FP64 the shared-memory form (bound by
+// the FP64 pipe, it gains nothing from registers and keeps three CTAs per SM).
+// In auto mode a thread-count override below what the register form needs
+// selects the shared form; with the register form requested it is an error.
+// The non-PIPG kernels of the plain form run with at most 512 threads.
+struct Plan {
+  int T;   // threads of the solve kernel (and of k_plain_pipg)
+  int Tr;  // threads of the other plain-form kernels
+  int pv;  // 1 shared-memory PIPG, 2 register PIPG
+};
+
+static bool plan_for(const pdg_handle* h, int N, Plan* out, std::string* why, bool use_override = true) {
+  const int treg = pipg_reg_threads(N, h->p.nu);
+  const int maxt = h->p.precision == 1 ? PDG_REG_MAXT_F32 : 512;
+  const int ov = use_override ? h->threads_override : 0;
+  int pv = h->pipg_variant;
+  if (pv == 0) pv = (h->p.precision == 1 && treg <= maxt && (ov == 0 || ov >= treg)) ? 2 : 1;
+  if (pv == 2) {
+    const int T = ov > 0 ? ov : treg;
+    if (T < treg || T > maxt) {
+      *why = "the register PIPG form needs " + std::to_string(treg) + " to " + std::to_string(maxt) +
+             " threads per CTA at N = " + std::to_string(N);
+      return false;
+    }
+    *out = {T, T < 512 ? T : 512, 2};
+  } else {
+    const int T = ov > 0 ? ov : threads_for(N, h->p.nu, h->p.precision);
+    if (T > 512) { *why = "the shared-memory PIPG form runs at most 512 threads per CTA"; return false; }
+    *out = {T, T, 1};
+  }
+  return true;
 }
+
+template <typename R, int NU>
+using PersistentFn = void (*)(const DParams, int, int, const double*, const int*, double*, double*, double*, double*,
+                              int*, int*, long long*, int*, int*, double*, int, const int*, const int*, int);
+template <typename R, int NU>
+using PlainPipgFn = void (*)(const DParams, int, int, const int*, PlainWs, const int*);
+template <typename R, int NU>
+static PersistentFn<R, NU> persistent_fn(int pv) { return pv == 2 ? k_persistent<R, NU, 2> : k_persistent<R, NU, 1>; }
+template <typename R, int NU>
+static PlainPipgFn<R, NU> plain_pipg_fn(int pv) { return pv == 2 ? k_plain_pipg<R, NU, 2> : k_plain_pipg<R, NU, 1>; }
 
 template <typename R, int NU>
 struct Kern {
   static int prepare(pdg_handle* h, int threads, size_t smem) {
-    const void* fns[] = {(const void*)k_persistent<R, NU>, (const void*)k_plain_init<R, NU>, (const void*)k_plain_disc<R, NU>,
-                         (const void*)k_plain_power<R, NU>, (const void*)k_plain_pipg<R, NU>, (const void*)k_plain_update<R, NU>,
+    const void* fns[] = {(const void*)k_persistent<R, NU, 1>, (const void*)k_persistent<R, NU, 2>,
+                         (const void*)k_plain_init<R, NU>, (const void*)k_plain_disc<R, NU>,
+                         (const void*)k_plain_power<R, NU>, (const void*)k_plain_pipg<R, NU, 1>,
+                         (const void*)k_plain_pipg<R, NU, 2>, (const void*)k_plain_update<R, NU>,
                          (const void*)k_subproblem<R, NU>};
     for (const void* f : fns) PDG_CUDA(h, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return 0;
@@ -702,17 +791,23 @@ struct Kern {
 template <typename R, int NU>
 static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int mode, double* X, double* U, double* tf,
                      double* fuel, int* status, int* scp_iters, long long* pipg_iters, int* trace, cudaStream_t s) {
-  const int T = pick_threads(h);
+  Plan pl;
+  std::string why;
+  if (!plan_for(h, h->n_max, &pl, &why)) return fail(h, PDG_EINVAL, why);
+  const int T = pl.T;
   const Lay L = make_lay(h->n_max, NU, T);
   const size_t smem = (size_t)L.total * sizeof(R);
-  if (L.ipw < 1) return fail(h, PDG_EINVAL, "threads per CTA too small for one discretization interval");
+  if (L.ipw < 1 || make_lay(h->n_max, NU, pl.Tr).ipw < 1)
+    return fail(h, PDG_EINVAL, "threads per CTA too small for one discretization interval");
   if (int rc = Kern<R, NU>::prepare(h, T, smem)) return rc;
+  const PersistentFn<R, NU> kp = persistent_fn<R, NU>(pl.pv);
   int occ = 0;
-  PDG_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persistent<R, NU>, T, smem));
+  PDG_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kp, T, smem));
   if (occ < 1) return fail(h, PDG_EINVAL, "solve kernel does not fit on an SM with this configuration");
   h->last_threads = T;
   h->last_ctas = occ;
   h->last_smem = (int)smem;
+  h->last_variant = pl.pv;
   // integer workspace: st, sit, pow_it, pipg_it [B each], done, queue
   const size_t nints = (size_t)4 * B + 2;
   if (h->ints_count < nints) {
@@ -726,8 +821,8 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
   if (mode == 1 || (mode == 2 && !Ns)) {
     PDG_CUDA(h, cudaMemsetAsync(queue, 0, sizeof(int), s));
     const int grid = (int)((long long)occ * h->num_sms < B ? (long long)occ * h->num_sms : B);
-    k_persistent<R, NU><<<grid, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, X, U, tf, fuel, status, scp_iters, pipg_iters,
-                                              trace, queue, h->rec_ptr, h->rec_stride, nullptr, nullptr, 0);
+    kp<<<grid, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, X, U, tf, fuel, status, scp_iters, pipg_iters, trace, queue,
+                             h->rec_ptr, h->rec_stride, nullptr, nullptr, 0);
     PDG_CUDA(h, cudaGetLastError());
     return 0;
   }
@@ -750,13 +845,15 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
     PDG_CUDA(h, cudaGetLastError());
     PDG_CUDA(h, cudaEventRecord(h->ev_in, s));
     for (int N = h->n_max; N >= 2; --N) {
-      const int Tn = h->threads_override > 0 && N == h->n_max ? h->threads_override
-                                                               : threads_for(N, NU, h->p.precision);
+      Plan pn;
+      if (!plan_for(h, N, &pn, &why, N == h->n_max)) return fail(h, PDG_EINVAL, why);
+      const int Tn = pn.T;
+      const PersistentFn<R, NU> kpn = persistent_fn<R, NU>(pn.pv);
       const Lay Ln = make_lay(N, NU, Tn);
       const size_t smem_n = (size_t)Ln.total * sizeof(R);
       if (Ln.ipw < 1) continue;
       int occ_n = 0;
-      PDG_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_n, k_persistent<R, NU>, Tn, smem_n));
+      PDG_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_n, kpn, Tn, smem_n));
       if (occ_n < 1) return fail(h, PDG_EINVAL, "a shape class does not fit on an SM");
       cudaStream_t cs = h->cls_streams[N];
       if (!cs) {
@@ -766,9 +863,8 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
       }
       PDG_CUDA(h, cudaStreamWaitEvent(cs, h->ev_in, 0));
       const int grid = (int)((long long)occ_n * h->num_sms < B ? (long long)occ_n * h->num_sms : B);
-      k_persistent<R, NU><<<grid, Tn, smem_n, cs>>>(h->dp, B, h->n_max, x0, Ns, X, U, tf, fuel, status, scp_iters,
-                                                    pipg_iters, trace, queues + N, h->rec_ptr, h->rec_stride, perm,
-                                                    class_off, N);
+      kpn<<<grid, Tn, smem_n, cs>>>(h->dp, B, h->n_max, x0, Ns, X, U, tf, fuel, status, scp_iters, pipg_iters, trace,
+                                    queues + N, h->rec_ptr, h->rec_stride, perm, class_off, N);
       PDG_CUDA(h, cudaGetLastError());
       PDG_CUDA(h, cudaEventRecord(h->cls_events[N], cs));
       PDG_CUDA(h, cudaStreamWaitEvent(s, h->cls_events[N], 0));
@@ -813,16 +909,18 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
   W.done = h->ints + 4 * (size_t)B;
   W.lit = h->lit;
   PDG_CUDA(h, cudaMemsetAsync(W.done, 0, sizeof(int), s));
-  k_plain_init<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, W, X, U, tf, fuel, status, scp_iters, pipg_iters);
+  const int Tr = pl.Tr;
+  const PlainPipgFn<R, NU> kpp = plain_pipg_fn<R, NU>(pl.pv);
+  k_plain_init<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, x0, Ns, W, X, U, tf, fuel, status, scp_iters, pipg_iters);
   PDG_CUDA(h, cudaGetLastError());
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   PDG_CUDA(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  k_plain_disc<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W);
-  k_plain_power<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
-  k_plain_pipg<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
-  k_plain_update<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, 0, X, U, tf, fuel, status, scp_iters, pipg_iters,
-                                            trace, nullptr);
+  k_plain_disc<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W);
+  k_plain_power<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
+  kpp<<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
+  k_plain_update<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W, 0, X, U, tf, fuel, status, scp_iters, pipg_iters,
+                                             trace, nullptr);
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   if (ce != cudaSuccess) return fail(h, PDG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
   ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -850,7 +948,10 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
 template <typename R, int NU>
 static int run_subproblem(pdg_handle* h, int B, const double* x0, const int* Ns, const double* X, const double* U,
                           double* Am, double* Bm, double* Bp, double* w, cudaStream_t s) {
-  const int T = pick_threads(h);
+  Plan pl;
+  std::string why;
+  if (!plan_for(h, h->n_max, &pl, &why)) return fail(h, PDG_EINVAL, why);
+  const int T = pl.Tr;
   const Lay L = make_lay(h->n_max, NU, T);
   const size_t smem = (size_t)L.total * sizeof(R);
   if (int rc = Kern<R, NU>::prepare(h, T, smem)) return rc;
@@ -863,7 +964,12 @@ template <typename R, int NU>
 static int run_step(pdg_handle* h, int B, const double* x0, const int* Ns, double* X, double* U, double* xh, double* uh,
                     double* mup, double* mum, double* phi, double* th, const int* force, double* sigma, double* defect,
                     double* step, int* iters, cudaStream_t s) {
-  const int T = pick_threads(h);
+  Plan pl;
+  std::string why;
+  if (!plan_for(h, h->n_max, &pl, &why)) return fail(h, PDG_EINVAL, why);
+  const int T = pl.T, Tr = pl.Tr;
+  const PlainPipgFn<R, NU> kpp = plain_pipg_fn<R, NU>(pl.pv);
+  h->last_variant = pl.pv;
   const Lay L = make_lay(h->n_max, NU, T);
   const size_t smem = (size_t)L.total * sizeof(R);
   if (int rc = Kern<R, NU>::prepare(h, T, smem)) return rc;
@@ -901,11 +1007,11 @@ static int run_step(pdg_handle* h, int B, const double* x0, const int* Ns, doubl
   W.done = h->ints + 4 * (size_t)B;
   W.lit = h->lit;
   k_pack<R, NU><<<B, 128, 0, s>>>(B, h->n_max, T, x0, Ns, W, 0, X, U, xh, uh, mup, mum, phi, th, sigma, defect, iters);
-  k_plain_disc<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W);
-  k_plain_power<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, force);
-  k_plain_pipg<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, force);
-  k_plain_update<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, 1, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                            nullptr, nullptr, nullptr, step);
+  k_plain_disc<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W);
+  k_plain_power<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W, force);
+  kpp<<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, force);
+  k_plain_update<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W, 1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                             nullptr, nullptr, nullptr, step);
   k_pack<R, NU><<<B, 128, 0, s>>>(B, h->n_max, T, x0, Ns, W, 1, X, U, xh, uh, mup, mum, phi, th, sigma, defect, iters);
   PDG_CUDA(h, cudaGetLastError());
   return 0;
@@ -935,7 +1041,11 @@ static int noalloc_scratch(pdg_handle* h, void** out) {
 template <typename R, int NU>
 static int run_noalloc(pdg_handle* h, int B, const double* x0, const int* Ns, double* X, double* U, double* tf,
                        double* fuel, int* status, int* scp_iters, long long* pipg_iters, cudaStream_t s) {
-  const int T = pick_threads(h);
+  Plan pl;
+  std::string why;
+  if (!plan_for(h, h->n_max, &pl, &why)) return fail(h, PDG_EINVAL, why);
+  const int T = pl.T, Tr = pl.Tr;
+  const PlainPipgFn<R, NU> kpp = plain_pipg_fn<R, NU>(pl.pv);
   const Lay L = make_lay(h->n_max, NU, T);
   const size_t smem = (size_t)L.total * sizeof(R);
   if (L.ipw < 1) return fail(h, PDG_EINVAL, "threads per CTA too small for one discretization interval");
@@ -969,17 +1079,18 @@ static int run_noalloc(pdg_handle* h, int B, const double* x0, const int* Ns, do
   // the array keeps the previous call's contents: clear the counter (every
   // per-instance field is written by k_plain_init before it is read)
   PDG_CUDA(h, cudaMemsetAsync(W.done, 0, sizeof(int), s));
-  k_plain_init<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, x0, Ns, W, X, U, tf, fuel, status, scp_iters, pipg_iters);
+  k_plain_init<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, x0, Ns, W, X, U, tf, fuel, status, scp_iters, pipg_iters);
   for (int j = 0; j < h->p.scp_jmax; ++j) {
-    k_plain_disc<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W);
-    k_plain_power<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
-    k_plain_pipg<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
-    k_plain_update<R, NU><<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, 0, X, U, tf, fuel, status, scp_iters,
-                                              pipg_iters, nullptr, nullptr);
+    k_plain_disc<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W);
+    k_plain_power<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
+    kpp<<<B, T, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
+    k_plain_update<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W, 0, X, U, tf, fuel, status, scp_iters,
+                                               pipg_iters, nullptr, nullptr);
   }
   PDG_CUDA(h, cudaGetLastError());
   h->last_threads = T;
   h->last_smem = (int)smem;
+  h->last_variant = pl.pv;
   return 0;
 }
 
@@ -1192,9 +1303,19 @@ int pdg_mc_launch_info(pdg_handle* h, int* threads, int* ctas_per_sm, int* smem_
   return PDG_OK;
 }
 
+int pdg_mc_set_pipg_form(pdg_handle* h, int form) {
+  if (!h) return PDG_EINVAL;
+  if (form < 0 || form > 2) return fail(h, PDG_EINVAL, "PIPG form must be 0 (auto), 1 (shared memory) or 2 (registers)");
+  h->pipg_variant = form;
+  return PDG_OK;
+}
+
+int pdg_mc_pipg_form(const pdg_handle* h) { return h ? h->last_variant : PDG_EINVAL; }
+
 int pdg_mc_set_threads(pdg_handle* h, int threads) {
   if (!h) return PDG_EINVAL;
-  if (threads < 0 || threads > 512 || (threads % 32) != 0) return fail(h, PDG_EINVAL, "threads must be 0 or a multiple of 32 up to 512");
+  if (threads < 0 || threads > PDG_REG_MAXT_F32 || (threads % 32) != 0)
+    return fail(h, PDG_EINVAL, "threads must be 0 or a multiple of 32 up to 640");
   h->threads_override = threads;
   return PDG_OK;
 }

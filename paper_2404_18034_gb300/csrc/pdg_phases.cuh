@@ -570,6 +570,302 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
   return j > jmax ? jmax : j;
 }
 
+// ---------------------------------------------------------------------------
+// PIPG_custom with the blocks and the iterates held in registers.
+//
+// The same iteration as phase_pipg (Alg. PIPG_custom with the stop test of
+// Alg. stopping), mapped so that nothing but the two exchanged vectors goes
+// through shared memory in the loop.  Thread roles are warp-uniform:
+//  * row threads p < RT = round32((N-1) NX): x task p (node p/NX + 1,
+//    component i = p%NX; it keeps column i of hat A^-_{node}) and dual row p
+//    (interval p/NX, row i; it keeps row i of hat A^-, hat B^-, hat B^+, hat w
+//    and its mu+-, phi entries).  Threads p < NX also own node 1.
+//  * control threads v = tid - RT < UT = round32(N G): node v/G, control
+//    component v%G (G lanes per node so a node's thrust is one aligned lane
+//    group for the cone projection); they keep column v%G of hat B^-_{node}
+//    and hat B^+_{node-1}.  In the dual step threads v < N-1 own theta_v.
+// Exchanged through shared memory: the relaxed dual (phi~, theta~) read by the
+// primal step and the extrapolated primal (2 z_{j+1} - z~_j) read by the dual
+// step, node vectors padded to 16 entries so they load as 16-byte vectors.
+// Needs blockDim.x >= pipg_reg_threads(N, NU).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int pipg_reg_groups(int nu) { return nu <= 4 ? 4 : 8; }
+__host__ __device__ inline int pipg_reg_threads(int N, int nu) {
+  return round32((N - 1) * NX) + round32(N * pipg_reg_groups(nu));
+}
+
+template <typename R> struct Vec16B;
+template <> struct Vec16B<float> {
+  static constexpr int n = 4;
+  __device__ __forceinline__ static void ld(const float* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <> struct Vec16B<double> {
+  static constexpr int n = 2;
+  __device__ __forceinline__ static void ld(const double* p, double* o) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+
+// Shared-memory offsets of the exchange vectors (inside the phase-local union
+// region, 16-byte aligned): vp[(N-1)][16], vt[32 + N], dx[N][16], du[N][NUP].
+struct RegLay { int vp, vt, dx, du, end; };
+__host__ __device__ inline RegLay make_reg_lay(const Lay& L) {
+  const int nup = L.nu <= 4 ? 4 : 8;
+  RegLay Q;
+  int o = (L.xt + 3) & ~3;
+  Q.vp = o; o += (L.N - 1) * 16;
+  Q.vt = o; o += (L.N + 3) & ~3;
+  Q.dx = o; o += L.N * 16;
+  Q.du = o; o += L.N * nup;
+  Q.end = o;
+  return Q;
+}
+
+// g + sum_{r < NX} a[r] v[r] with v read from shared memory in 16-byte pieces
+// (four interleaved accumulators; v is 16-byte aligned, v[15] is padding)
+template <typename R>
+__device__ __forceinline__ R dot15_sm(const R (&a)[NX], const R* v, R g) {
+  constexpr int W = Vec16B<R>::n;
+  R h[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 16; q += W) {
+    R c[W];
+    Vec16B<R>::ld(v + q, c);
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      if (q + e < NX) h[(q + e) & 3] = fma(a[q + e], c[e], h[(q + e) & 3]);
+    }
+  }
+  return g + ((h[0] + h[1]) + (h[2] + h[3]));
+}
+
+// Out of line by default: the loop then gets the whole register file, not
+// what the enclosing kernel leaves over.  The shared-memory image is reached
+// through the kernel's dynamic shared array (every kernel places the image at
+// its start), so the accesses stay shared-memory loads and stores.
+#ifdef PDG_PIPG_REG_NOINLINE
+#define PDG_PREG_ATTR __noinline__
+#else
+#define PDG_PREG_ATTR __forceinline__
+#endif
+template <typename R, int NU>
+__device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /*image*/, R sigma, int force) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* const sm = reinterpret_cast<R*>(smraw);
+  constexpr int G = NU <= 4 ? 4 : 8;
+  constexpr int NUP = NU <= 4 ? 4 : 8;
+  const int N = L.N, tid = threadIdx.x;
+  const int nm = (N - 1) * NX;
+  const int RT = round32(nm), UT = round32(N * G);
+  const RegLay Q = make_reg_lay(L);
+  R* const vp = sm + Q.vp;
+  R* const vt = sm + Q.vt;
+  R* const dxs = sm + Q.dx;
+  R* const dus = sm + Q.du;
+  const bool row = tid < RT;
+  const bool ctl = !row && tid < RT + UT;
+  // row thread p = tid: dual row (interval kd, row i) and x task (node kx = kd + 1, component i)
+  const int kd = tid / NX, i = tid - NX * (tid / NX);
+  const int kx = kd + 1;
+  const bool has_d = row && tid < nm;                 // x task exists exactly when the dual row does
+  const bool has_colA = has_d && kx <= N - 2;
+  const bool last_x = has_d && kx == N - 1;
+  // control thread v: node ku, component cc; theta_v for v < N-1; node-1 entry v for v < NX
+  const int v = tid - RT;
+  const int ku = v / G, cc = v - G * (v / G);
+  const bool has_u = ctl && ku < N && cc < NU;
+  const bool has_th = ctl && v < N - 1;
+  const bool has_x1 = ctl && v < NX;
+  // registers.  Arrays: column of hat A^-_{kx} / row of hat A^-_{kd} / row of
+  // hat B^-, hat B^+ (row thread); column of hat B^-_{ku} / of hat B^+_{ku-1}
+  // (control thread).  Scalars by role:
+  //   row:     r0 x~, r1 x_hat, r2 nu+, r3 nu-, r4 mu+, r5 mu-, r6 phi~, r7 phi, r8 hat w
+  //   control: r0 u~, r1 u_hat, r2 lo, r3 hi, r4 reference thrust,
+  //            r5 theta~, r6 theta, r7 hat eps, r8 x~ node 1, r9 x_hat node 1, r10 hat z_i
+  R a1[NX], a2[NX], a3[2 * NU];
+  R r0 = 0, r1 = 0, r2 = 0, r3 = 0, r4 = 0, r5 = 0, r6 = 0, r7 = 0, r8 = 0, r9 = 0, r10 = 0;
+#pragma unroll
+  for (int r = 0; r < NX; ++r) { a1[r] = 0; a2[r] = 0; }
+#pragma unroll
+  for (int r = 0; r < 2 * NU; ++r) a3[r] = 0;
+  if (has_d) {
+    r0 = r1 = sm[L.xh + kx * NX + i];
+    if (has_colA) {
+#pragma unroll
+      for (int r = 0; r < NX; ++r) a1[r] = sm[L.Am + (kx * NX + r) * NX + i];
+    }
+#pragma unroll
+    for (int c = 0; c < NX; ++c) a2[c] = sm[L.Am + (kd * NX + i) * NX + c];
+#pragma unroll
+    for (int c = 0; c < NU; ++c) {
+      a3[c] = sm[L.Bm + (kd * NX + i) * NU + c];
+      a3[NU + c] = sm[L.Bp + (kd * NX + i) * NU + c];
+    }
+    r8 = sm[L.w + tid];
+    r4 = r2 = sm[L.mup + tid];
+    r5 = r3 = sm[L.mum + tid];
+    r7 = r6 = sm[L.phi + tid];
+    vp[kd * 16 + i] = r6;
+  }
+  if (has_u) {
+    r0 = r1 = sm[L.uh + ku * NU + cc];
+    if (ku <= N - 2) {
+#pragma unroll
+      for (int r = 0; r < NX; ++r) a1[r] = sm[L.Bm + (ku * NX + r) * NU + cc];
+    }
+    if (ku >= 1) {
+#pragma unroll
+      for (int r = 0; r < NX; ++r) a2[r] = sm[L.Bp + ((ku - 1) * NX + r) * NU + cc];
+    }
+    if (cc == NU - 1) { r2 = sm[L.lo + ku]; r3 = sm[L.hi + ku]; }
+    if (cc < 3) r4 = sm[L.Ub + ku * NU + cc];
+  }
+  if (has_th) {
+    r6 = r5 = sm[L.th + v];
+    r7 = sm[L.eps + v];
+    vt[v] = r5;
+  }
+  if (has_x1) { r8 = r9 = sm[L.xh + v]; r10 = sm[L.zi + v]; }
+  __syncthreads();
+  const R wp = R(P.w_prox);
+  const R alpha = R(2) / (wp + sqrt(wp * wp + R(4) * R(P.omega) * sigma));
+  const R beta = R(P.omega) * alpha;
+  const R c1 = R(1) - alpha * wp;
+  const R rho = R(P.rho);
+  const R rb = rho * beta;
+  const R wep = R(P.w_ep);
+  const int jmax = force > 0 ? force : P.pipg_jmax;
+  const int jcheck = P.pipg_jcheck;
+  int j;
+  for (j = 1; j <= jmax; ++j) {
+    const bool chk = force <= 0 && jcheck > 0 && (j % jcheck) == 0;
+    R zn = 0, zo = 0, zd = 0, rn = 0, ro = 0, rd = 0;
+    // ---- projected gradient step (primal)
+    if (has_d) {
+      R G = -vp[kd * 16 + i];
+      if (has_colA) {
+        G = dot15_sm(a1, vp + kx * 16, G);
+        if (i == IY) G -= vt[kx];
+      }
+      if (i == IY) G += vt[kd];
+      if (last_x && i == IM) G -= R(P.w_cost);
+      R xn = c1 * r0 - alpha * G;
+      if (last_x && P.fix_f[i]) xn = sm[L.zf + i];
+      dxs[kx * 16 + i] = R(2) * xn - r0;
+      r0 += rho * (xn - r0);
+      if (chk) { zn = rmax(zn, fabs(xn)); zo = rmax(zo, fabs(r1)); zd = rmax(zd, fabs(xn - r1)); }
+      r1 = xn;
+    } else if (ctl) {
+      R un = 0;
+      if (has_u) {
+        R Gs = 0;
+        if (ku <= N - 2) Gs = dot15_sm(a1, vp + ku * 16, Gs);
+        if (ku >= 1) Gs = dot15_sm(a2, vp + (ku - 1) * 16, Gs);
+        un = c1 * r0 - alpha * Gs;
+        if (cc == NU - 1) un = rmin(rmax(un, r2), r3);
+      }
+      if (P.soc) {
+        // the node's thrust onto the sector: cone about body x, then the ball
+        const R sa = R(P.soc_tan), tmax = R(P.T_max), pT = R(P.Pu[0]), ipT = R(P.Puinv[0]);
+        const R tv = (has_u && cc < 3) ? r4 + pT * un : R(0);
+        const int base = (tid & 31) & ~(G - 1);
+        R T0 = __shfl_sync(0xffffffffu, tv, base);
+        R T1 = __shfl_sync(0xffffffffu, tv, base + 1);
+        R T2 = __shfl_sync(0xffffffffu, tv, base + 2);
+        const R rr = sqrt(T1 * T1 + T2 * T2);
+        if (rr > sa * T0) {
+          if (sa * rr <= -T0) {
+            T0 = 0; T1 = 0; T2 = 0;
+          } else {
+            const R tp = (T0 + sa * rr) / (R(1) + sa * sa);
+            const R sc = sa * tp / rr;
+            T0 = tp; T1 *= sc; T2 *= sc;
+          }
+        }
+        const R nT = sqrt(T0 * T0 + T1 * T1 + T2 * T2);
+        if (nT > tmax) { const R q = tmax / nT; T0 *= q; T1 *= q; T2 *= q; }
+        if (has_u && cc < 3) un = ((cc == 0 ? T0 : (cc == 1 ? T1 : T2)) - r4) * ipT;
+      }
+      if (has_u) {
+        dus[ku * NUP + cc] = R(2) * un - r0;
+        r0 += rho * (un - r0);
+        if (chk) { zn = rmax(zn, fabs(un)); zo = rmax(zo, fabs(r1)); zd = rmax(zd, fabs(un - r1)); }
+        r1 = un;
+      }
+      if (has_x1) {  // node 1: every component fixed by E_i
+        dxs[v] = R(2) * r10 - r8;
+        r8 += rho * (r10 - r8);
+        if (chk) { zn = rmax(zn, fabs(r10)); zo = rmax(zo, fabs(r9)); zd = rmax(zd, fabs(r10 - r9)); }
+        r9 = r10;
+      }
+    }
+    __syncthreads();
+    // ---- virtual controls and proportional-integral feedback (dual)
+    if (has_d) {
+      const R mp = max0(r2 - alpha * (wep + r6));
+      const R mm = max0(r3 - alpha * (wep - r6));
+      const R a = r2, b = r3;
+      r2 = a + rho * (mp - a);
+      r3 = b + rho * (mm - b);
+      if (chk) {
+        zn = rmax(zn, rmax(mp, mm)); zo = rmax(zo, rmax(r4, r5));
+        zd = rmax(zd, rmax(fabs(mp - r4), fabs(mm - r5)));
+      }
+      r4 = mp;
+      r5 = mm;
+      R r = r8 + ((R(2) * mp - a) - (R(2) * mm - b)) - dxs[kx * 16 + i];
+      r = dot15_sm(a2, dxs + kd * 16, r);
+      R r2b = 0;
+#pragma unroll
+      for (int c0 = 0; c0 < NU; c0 += Vec16B<R>::n) {
+        R d0[Vec16B<R>::n], d1[Vec16B<R>::n];
+        Vec16B<R>::ld(dus + kd * NUP + c0, d0);
+        Vec16B<R>::ld(dus + kx * NUP + c0, d1);
+#pragma unroll
+        for (int e = 0; e < Vec16B<R>::n; ++e) {
+          if (c0 + e < NU) { r = fma(a3[c0 + e], d0[e], r); r2b = fma(a3[NU + c0 + e], d1[e], r2b); }
+        }
+      }
+      r += r2b;
+      const R pn = r6 + beta * r;
+      r6 += rb * r;  // = phi~ + rho (phi_new - phi~)
+      if (chk) { rn = rmax(rn, fabs(pn)); ro = rmax(ro, fabs(r7)); rd = rmax(rd, fabs(pn - r7)); }
+      r7 = pn;
+      vp[kd * 16 + i] = r6;
+    } else if (has_th) {
+      const R hy = dxs[(v + 1) * 16 + IY] - dxs[v * 16 + IY] - r7;
+      const R tn = max0(r5 + beta * hy);
+      r5 += rho * (tn - r5);
+      if (chk) { rn = rmax(rn, tn); ro = rmax(ro, fabs(r6)); rd = rmax(rd, fabs(tn - r6)); }
+      r6 = tn;
+      vt[v] = r5;
+    }
+    if (chk) {
+      R w6[6] = {zn, zo, zd, rn, ro, rd};
+      block_max_k<R, 6>(w6, sm + L.red);
+      if (w6[2] <= R(P.eps_abs) + R(P.eps_rel) * rmax(w6[0], w6[1]) &&
+          w6[5] <= R(P.eps_abs) + R(P.eps_rel) * rmax(w6[3], w6[4]))
+        break;
+    } else {
+      __syncthreads();
+    }
+  }
+  // iterates back to the image (warm start of the next SCP iteration)
+  if (has_d) {
+    sm[L.xh + kx * NX + i] = r1;
+    sm[L.mup + tid] = r4; sm[L.mum + tid] = r5; sm[L.phi + tid] = r7;
+  }
+  if (has_u) sm[L.uh + ku * NU + cc] = r1;
+  if (has_th) sm[L.th + v] = r6;
+  if (has_x1) sm[L.xh + v] = r9;
+  __syncthreads();
+  return j > jmax ? jmax : j;
+}
+
 // SCP update (Sec. 2.3.2: x = P_x x_hat + xbar) and convergence test
 // (reading: scaled step, scaled defect and CTCS budget).  Returns the scaled
 // step; *nonfinite is set when X or U holds a non-finite value.

@@ -23,7 +23,7 @@ ERRORS = {-1: "PDG_EINVAL", -2: "PDG_ENOMEM", -3: "PDG_ECUDA"}
 EXPORTS = ("pdg_mc_init", "pdg_mc_destroy", "pdg_mc_last_error", "pdg_mc_solve_batch",
            "pdg_mc_solve_batch_host", "pdg_mc_subproblem", "pdg_mc_scp_step", "pdg_mc_launch_info",
            "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc",
-           "pdg_mc_grad_batch")
+           "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form")
 
 
 class PdgParams(C.Structure):
@@ -75,8 +75,11 @@ def load_library(path: str = LIB_PATH):
     L.pdg_mc_probe_fma.argtypes = [C.c_int, C.POINTER(C.c_double), _VP]
     L.pdg_mc_solve_batch_noalloc.argtypes = [_VP, C.c_int, _VP, _VP] + [_VP] * 7 + [_VP]
     L.pdg_mc_grad_batch.argtypes = [_VP, C.c_int] + [_VP] * 8 + [_VP]
+    L.pdg_mc_set_pipg_form.argtypes = [_VP, C.c_int]
+    L.pdg_mc_pipg_form.argtypes = [_VP]
     for name in ("pdg_mc_init", "pdg_mc_solve_batch", "pdg_mc_solve_batch_host", "pdg_mc_subproblem",
-                 "pdg_mc_scp_step", "pdg_mc_launch_info", "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc", "pdg_mc_grad_batch"):
+                 "pdg_mc_scp_step", "pdg_mc_launch_info", "pdg_mc_set_threads", "pdg_mc_probe_fma",
+                 "pdg_mc_solve_batch_noalloc", "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -141,14 +144,17 @@ class Solver:
             raise RuntimeError(f"pdg_mc_init: {ERRORS.get(rc, rc)}: {self.lib.pdg_mc_last_error(None).decode()}")
         self.h = h
         self.tuned_threads = None
+        self.tuned_form = None
         if tune_cache:
             import torch
 
             from .autotune import lookup
-            t = lookup(torch.cuda.get_device_name(), self.n_max, self.nu, self.precision, mode, tune_cache)
-            if t:
-                self.set_threads(t)
-                self.tuned_threads = t
+            e = lookup(torch.cuda.get_device_name(), self.n_max, self.nu, self.precision, mode, tune_cache)
+            if e:
+                self.set_pipg_form(e[1])
+                self.set_threads(e[0])
+                self.tuned_threads = e[0]
+                self.tuned_form = e[1]
 
     def close(self):
         if getattr(self, "h", None):
@@ -267,7 +273,12 @@ class Solver:
     def launch_info(self):
         t, c, s = C.c_int(), C.c_int(), C.c_int()
         self._check(self.lib.pdg_mc_launch_info(self.h, C.byref(t), C.byref(c), C.byref(s)), "pdg_mc_launch_info")
-        return dict(threads=t.value, ctas_per_sm=c.value, smem_bytes=s.value)
+        return dict(threads=t.value, ctas_per_sm=c.value, smem_bytes=s.value,
+                    pipg_form=int(self.lib.pdg_mc_pipg_form(self.h)))
+
+    def set_pipg_form(self, form: int):
+        """0 automatic, 1 blocks in shared memory, 2 blocks in registers."""
+        self._check(self.lib.pdg_mc_set_pipg_form(self.h, int(form)), "pdg_mc_set_pipg_form")
 
     def set_threads(self, threads: int):
         self._check(self.lib.pdg_mc_set_threads(self.h, int(threads)), "pdg_mc_set_threads")

@@ -22,10 +22,14 @@ def torch_cuda():
     return torch
 
 
-def _solver(inputs, nu=4, n_max=15, precision=0, **ov):
+def _solver(inputs, nu=4, n_max=15, precision=0, form=0, **ov):
+    """form: PIPG layout (0 automatic, 1 shared memory, 2 registers)."""
     from paper_2404_18034_gb300.pdg_mc import Solver
     p = inputs.load_params(nu=nu, **ov)
-    return p, Solver(p, n_max, precision)
+    S = Solver(p, n_max, precision)
+    if form:
+        S.set_pipg_form(form)
+    return p, S
 
 
 def _refs(O, inputs, p, B, Ns, seed, perturb=0.03):
@@ -67,13 +71,14 @@ def test_subproblem_blocks(torch_cuda, oracle, inputs, nu, prec):
         assert np.all(o["Am"][b, N - 1:].cpu().numpy() == 0)
 
 
-@pytest.mark.parametrize("nu", [4, 7])
-def test_scp_step_forced_counts(torch_cuda, oracle, inputs, nu):
+@pytest.mark.parametrize("nu,form", [(4, 1), (7, 1), (4, 2), (7, 2)])
+def test_scp_step_forced_counts(torch_cuda, oracle, inputs, nu, form):
     """Three chained SCP iterations (discretize, scale, power iteration, PIPG
-    with the oracle's counts forced, update) match the oracle's iterations."""
+    with the oracle's counts forced, update) match the oracle's iterations,
+    with the PIPG loop in shared memory (form 1) and in registers (form 2)."""
     torch = torch_cuda
     Ns = np.array([15, 10, 4, 15], np.int32)
-    p, S = _solver(inputs, nu, 15)
+    p, S = _solver(inputs, nu, 15, form=form)
     B, n_max = len(Ns), 15
     x0 = inputs.dispersion(p, B, 5, "bj")
     X = np.zeros((B, n_max, 15)); U = np.zeros((B, n_max, nu))
@@ -106,6 +111,7 @@ def test_scp_step_forced_counts(torch_cuda, oracle, inputs, nu):
                 assert_scaled_close(g, ref, 1.0, what=f"{k} it{it} b{b}")
             assert abs(o["defect"][b].item() - r["defect"]) <= RTOL * max(r["defect"], 1.0)
             assert abs(o["step"][b].item() - r["step"]) <= RTOL * max(r["step"], 1.0)
+    assert S.launch_info()["pipg_form"] == form
 
 
 def _solve_and_replay(torch, oracle, inputs, p, S, x0, Ns, mode, sample):
@@ -139,6 +145,72 @@ def test_full_solve_matches_oracle_replay(torch_cuda, oracle, inputs, mode):
     Ns = inputs.node_counts(B, inputs.config_seed(2))
     o = _solve_and_replay(torch, oracle, inputs, p, S, x0, Ns, mode, range(B))
     assert np.mean(o["status"] == 0) >= 0.75  # the replayed sample above converges on both sides
+
+
+@pytest.mark.parametrize("mode", [1, 0, 2])
+def test_register_form_matches_oracle_replay(torch_cuda, oracle, inputs, mode):
+    """The register-resident PIPG form in FP64, whole solves on an uneven
+    batch (N in {10, 15, 20}; ragged rows and control lanes), every form of
+    execution, against the oracle replay at the FP64 tolerance."""
+    torch = torch_cuda
+    p, S = _solver(inputs, 4, 20, form=2)
+    B = 9
+    x0 = inputs.dispersion(p, B, 21, "bj")
+    Ns = np.array([10, 15, 20] * 3, np.int32)
+    o = _solve_and_replay(torch, oracle, inputs, p, S, x0, Ns, mode, range(B))
+    assert np.mean(o["status"] == 0) >= 0.75
+    assert S.launch_info()["pipg_form"] == 2
+
+
+def test_pipg_form_selection(torch_cuda, inputs):
+    """Automatic choice (registers for FP32, shared memory for FP64), the
+    thread-count rule of the register form, and rejected settings."""
+    torch = torch_cuda
+    p = inputs.load_params()
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    x0 = torch.from_numpy(inputs.dispersion(p, 2, 3, "bj")).cuda()
+    S64, S32 = Solver(p, 15, 0), Solver(p, 15, 1)
+    S64.solve(x0, mode=1); S32.solve(x0, mode=1)
+    torch.cuda.synchronize()
+    assert S64.launch_info()["pipg_form"] == 1 and S32.launch_info()["pipg_form"] == 2
+    assert S32.launch_info()["threads"] == 224 + 64
+    S32.set_threads(160)            # below the register form's need: automatic falls back
+    S32.solve(x0, mode=1)
+    torch.cuda.synchronize()
+    assert S32.launch_info()["pipg_form"] == 1
+    S32.set_pipg_form(2)            # ... and an explicit request is refused
+    with pytest.raises(RuntimeError, match="EINVAL"):
+        S32.solve(x0, mode=1)
+    with pytest.raises(RuntimeError, match="EINVAL"):
+        S64.set_pipg_form(3)
+    S64.set_pipg_form(2)
+    S64b = Solver(p, 30, 0)
+    S64b.set_pipg_form(2)           # FP64 register form: at most 512 threads (N = 30 needs 576)
+    with pytest.raises(RuntimeError, match="EINVAL"):
+        S64b.solve(torch.from_numpy(inputs.dispersion(p, 1, 3, "bj")).cuda(), mode=1)
+
+
+def test_fp32_register_form_tracks_shared_form(torch_cuda, oracle, inputs):
+    """FP32: the register form against the shared-memory form and against
+    FP64.  Both FP32 forms run the same iteration with different rounding, so
+    they are compared at the FP32 level on instances converged in both."""
+    torch = torch_cuda
+    p, S2 = _solver(inputs, 4, 15, precision=1, form=2)
+    _, S1 = _solver(inputs, 4, 15, precision=1, form=1)
+    _, S64 = _solver(inputs, 4, 15)
+    B = 32
+    x0 = torch.from_numpy(inputs.dispersion(p, B, 17, "bj")).cuda()
+    a, b, c = S2.solve(x0, mode=1), S1.solve(x0, mode=1), S64.solve(x0, mode=1)
+    torch.cuda.synchronize()
+    sa, sb, sc = (o["status"].cpu().numpy() for o in (a, b, c))
+    assert np.mean(sa == 0) >= 0.8 and np.mean(sb == 0) >= 0.8
+    both = np.nonzero((sa == 0) & (sb == 0) & (sc == 0))[0]
+    assert len(both) >= B // 2
+    for i in both:
+        for o, what in ((b, "fp32 shared"), (c, "fp64")):
+            assert_scaled_close(a["X"][i].cpu().numpy(), o["X"][i].cpu().numpy(), p["P_x"], rtol=2e-2,
+                                what=f"fp32 registers vs {what} X {i}")
+            assert abs(a["fuel"][i].item() - o["fuel"][i].item()) <= 2e-2 * p["P_x"][0]
 
 
 def test_nu7_solve_matches_oracle_replay(torch_cuda, oracle, inputs):
@@ -324,12 +396,12 @@ def test_budget_status(torch_cuda, inputs):
     assert np.all(out["status"].cpu().numpy() == PDG_BUDGET)
 
 
-@pytest.mark.parametrize("nu", [4, 7])
-def test_soc_variant_matches_oracle(torch_cuda, oracle, inputs, nu):
+@pytest.mark.parametrize("nu,form", [(4, 1), (7, 1), (4, 2)])
+def test_soc_variant_matches_oracle(torch_cuda, oracle, inputs, nu, form):
     """soc_thrust = 1 (thrust sector by projection inside PIPG): chained SCP
     steps with forced counts and full solves match the oracle replay."""
     torch = torch_cuda
-    p, S = _solver(inputs, nu, 15, soc_thrust=1)
+    p, S = _solver(inputs, nu, 15, form=form, soc_thrust=1)
     B, n_max = 3, 15
     x0 = inputs.dispersion(p, B, 12, "bj")
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
