@@ -143,6 +143,51 @@ __device__ __forceinline__ R block_sum(R v, R* red) {
   return s;
 }
 
+// Non-negative floating-point numbers order like their bit patterns, so the
+// maxima of the PIPG stop test (of |.|, mu >= 0, theta >= 0) are taken exactly
+// in integer arithmetic: on GB300 every FP64 warp instruction costs a slot of
+// the narrow FP64 pipe whatever its active lanes, integer ones do not.
+template <typename R> struct OrdBits;
+template <> struct OrdBits<double> {
+  using U = unsigned long long;
+  __device__ __forceinline__ static U abs(double x) { return U(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull; }
+  __device__ __forceinline__ static U nonneg(double x) { return U(__double_as_longlong(x)); }
+  __device__ __forceinline__ static double val(U u) { return __longlong_as_double((long long)u); }
+};
+template <> struct OrdBits<float> {
+  using U = unsigned int;
+  __device__ __forceinline__ static U abs(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
+  __device__ __forceinline__ static U nonneg(float x) { return __float_as_uint(x); }
+  __device__ __forceinline__ static float val(U u) { return __uint_as_float(u); }
+};
+template <typename U>
+__device__ __forceinline__ U umax(U a, U b) { return a > b ? a : b; }
+
+// Block-wide maxima of K unsigned values (every thread calls it; red holds
+// K * 32 values of U).
+template <typename U, int K>
+__device__ __forceinline__ void block_max_u(U (&v)[K], U* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] = umax(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) red[wid * K + q] = v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    U m = red[q];
+    for (int i = 1; i < nw; ++i) m = umax(m, red[i * K + q]);
+    v[q] = m;
+  }
+  __syncthreads();
+}
+
 template <typename R>
 __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 template <typename R>

@@ -121,10 +121,10 @@ __device__ PDG_DISC_ATTR R phase_discretize(const DParams& P, const Lay& L, R* s
             for (int i = 0; i < NX; ++i) { xA[i] = d[i]; xS[i] = xP[i] + h2 * d[i]; }
           } else if (sgi == 1) {
 #pragma unroll
-            for (int i = 0; i < NX; ++i) { xA[i] += R(2) * d[i]; xS[i] = xP[i] + h2 * d[i]; }
+            for (int i = 0; i < NX; ++i) { xA[i] = fma(R(2), d[i], xA[i]); xS[i] = xP[i] + h2 * d[i]; }
           } else if (sgi == 2) {
 #pragma unroll
-            for (int i = 0; i < NX; ++i) { xA[i] += R(2) * d[i]; xS[i] = xP[i] + h * d[i]; }
+            for (int i = 0; i < NX; ++i) { xA[i] = fma(R(2), d[i], xA[i]); xS[i] = xP[i] + h * d[i]; }
           } else {
 #pragma unroll
             for (int i = 0; i < NX; ++i) { const R v = xP[i] + h6 * (xA[i] + d[i]); xP[i] = v; xS[i] = v; }
@@ -140,10 +140,10 @@ __device__ PDG_DISC_ATTR R phase_discretize(const DParams& P, const Lay& L, R* s
             for (int i = 0; i < NX; ++i) { Ac[i] = d[i]; Sv[i] = Pv[i] + h2 * d[i]; }
           } else if (sgi == 1) {
 #pragma unroll
-            for (int i = 0; i < NX; ++i) { Ac[i] += R(2) * d[i]; Sv[i] = Pv[i] + h2 * d[i]; }
+            for (int i = 0; i < NX; ++i) { Ac[i] = fma(R(2), d[i], Ac[i]); Sv[i] = Pv[i] + h2 * d[i]; }
           } else if (sgi == 2) {
 #pragma unroll
-            for (int i = 0; i < NX; ++i) { Ac[i] += R(2) * d[i]; Sv[i] = Pv[i] + h * d[i]; }
+            for (int i = 0; i < NX; ++i) { Ac[i] = fma(R(2), d[i], Ac[i]); Sv[i] = Pv[i] + h * d[i]; }
           } else {
 #pragma unroll
             for (int i = 0; i < NX; ++i) { Pv[i] += h6 * (Ac[i] + d[i]); Sv[i] = Pv[i]; }
@@ -343,9 +343,14 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
 //     tasks) and the fixed node 1 (15 tasks);
 //   dual phase: row i of interval k updates mu^+-, nu^+- (they read the same
 //     extrapolated dual entry) and then phi; then the CTCS rows theta_k.
-// Returns the iterations run.
+template <bool B> struct ChkTag { static constexpr bool value = B; };
+
+// Returns the iterations run.  Extrapolations 2 z - z~ are written as fma:
+// the compiler would otherwise form z + z and subtract (two FP64 adds).
 template <typename R, int NU>
 __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force) {
+  using OB = OrdBits<R>;
+  using U = typename OB::U;
   const int N = L.N, T = blockDim.x, tid = threadIdx.x;
   constexpr int G = NU <= 4 ? 4 : 8;   // lanes per node for the control step
   const int nxk = (N - 1) * NX, nm = (N - 1) * NX;
@@ -374,29 +379,35 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
   R* vth = sm + L.vth;
   R* dx = sm + L.dx;
   R* du = sm + L.du;
-  for (int t = tid; t < N * NX + N * NU + 2 * nm + (N - 1); t += T) {
-    if (t < N * NX) xt[t] = xh[t];
-    else if (t < N * NX + N * NU) ut[t - N * NX] = uh[t - N * NX];
-    else if (t < N * NX + N * NU + nm) { const int q = t - N * NX - N * NU; nup[q] = mup[q]; num[q] = mum[q]; }
-    else if (t < N * NX + N * NU + 2 * nm) { const int q = t - N * NX - N * NU - nm; vph[q] = phi[q]; }
-    else { const int q = t - N * NX - N * NU - 2 * nm; vth[q] = th[q]; }
-  }
-  __syncthreads();
   const R wp = R(P.w_prox);
   const R alpha = R(2) / (wp + sqrt(wp * wp + R(4) * R(P.omega) * sigma));
   const R beta = R(P.omega) * alpha;
   const R c1 = R(1) - alpha * wp;
   const R rho = R(P.rho);
   const R rb = rho * beta;
-  const R wcost = R(P.w_cost), wep = R(P.w_ep);
-  const R eabs = R(P.eps_abs), erel = R(P.eps_rel);
+  const R wcost = R(P.w_cost);
+  // The relaxed virtual-control iterates are kept shifted by alpha w_ep
+  // (nu~ = nu - alpha w_ep): the projection max{0, nu - alpha (w_ep +- phi)}
+  // is then one FMA and the relaxation two; the shift cancels in the
+  // extrapolated difference (2 mu+ - nu+) - (2 mu- - nu-).
+  const R aw = alpha * R(P.w_ep);
+  const R omr = R(1) - rho, raw = rho * aw;
+  for (int t = tid; t < N * NX + N * NU + 2 * nm + (N - 1); t += T) {
+    if (t < N * NX) xt[t] = xh[t];
+    else if (t < N * NX + N * NU) ut[t - N * NX] = uh[t - N * NX];
+    else if (t < N * NX + N * NU + nm) { const int q = t - N * NX - N * NU; nup[q] = mup[q] - aw; num[q] = mum[q] - aw; }
+    else if (t < N * NX + N * NU + 2 * nm) { const int q = t - N * NX - N * NU - nm; vph[q] = phi[q]; }
+    else { const int q = t - N * NX - N * NU - 2 * nm; vth[q] = th[q]; }
+  }
+  __syncthreads();
   const R sa = R(P.soc_tan), tmax = R(P.T_max), pT = R(P.Pu[0]), ipT = R(P.Puinv[0]);
   const int jmax = force > 0 ? force : P.pipg_jmax;
   const int jcheck = P.pipg_jcheck;
-  int j;
-  for (j = 1; j <= jmax; ++j) {
-    const bool chk = force <= 0 && jcheck > 0 && (j % jcheck) == 0;
-    R zn = 0, zo = 0, zd = 0;
+  // One iteration; CHK (compile time) adds the stop test, so that the other
+  // iterations carry none of its instructions.  Returns true to stop.
+  auto iterate = [&](auto chk_tag) -> bool {
+    constexpr bool chk = decltype(chk_tag)::value;
+    U zn = 0, zo = 0, zd = 0;
     // ---- projected gradient step (primal)
     for (int t = tid; t < PX + PU; t += T) {
       if (t < PX) {
@@ -408,24 +419,19 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           if (k < N - 1) {
             const R* a = Am + k * NX * NX + i;
             const R* f = vph + k * NX;
-            R G2 = 0;
 #pragma unroll
-            for (int r = 0; r < NX; r += 2) {
-              G += a[r * NX] * f[r];
-              if (r + 1 < NX) G2 += a[(r + 1) * NX] * f[r + 1];
-            }
-            G += G2;
+            for (int r = 0; r < NX; ++r) G += a[r * NX] * f[r];
             if (i == IY) G -= vth[k];
           }
           if (i == IY) G += vth[k - 1];
           if (k == N - 1 && i == IM) G -= wcost;  // e_cost = -e_m (maximize m_N)
           R xn = c1 * xv - alpha * G;
           if (k == N - 1 && P.fix_f[i]) xn = zf[i];
-          dx[o] = R(2) * xn - xv;
+          dx[o] = fma(R(2), xn, -xv);
           xt[o] = xv + rho * (xn - xv);
-          if (chk) {
+          if constexpr (chk) {
             const R old = xh[o];
-            zn = rmax(zn, fabs(xn)); zo = rmax(zo, fabs(old)); zd = rmax(zd, fabs(xn - old));
+            zn = umax(zn, OB::abs(xn)); zo = umax(zo, OB::abs(old)); zd = umax(zd, OB::abs(xn - old));
           }
           xh[o] = xn;
         }
@@ -439,7 +445,7 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           R uv = 0, un = 0;
           if (valid) {
             uv = ut[o];
-            R Gs = 0, G2 = 0;
+            R Gs = 0;
             if (k < N - 1) {
               const R* a = Bm + k * NX * NU + cc;
               const R* f = vph + k * NX;
@@ -450,9 +456,8 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
               const R* a = Bp + (k - 1) * NX * NU + cc;
               const R* f = vph + (k - 1) * NX;
 #pragma unroll
-              for (int r = 0; r < NX; ++r) G2 += a[r * NU] * f[r];
+              for (int r = 0; r < NX; ++r) Gs += a[r * NU] * f[r];
             }
-            Gs += G2;
             un = c1 * uv - alpha * Gs;
             if (cc == NU - 1) un = rmin(rmax(un, lo[k]), hi[k]);
           }
@@ -465,7 +470,7 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
             R T0 = __shfl_sync(0xffffffffu, tv, base);
             R T1 = __shfl_sync(0xffffffffu, tv, base + 1);
             R T2 = __shfl_sync(0xffffffffu, tv, base + 2);
-            const R rr = sqrt(T1 * T1 + T2 * T2);
+            const R rr = ::sqrt(T1 * T1 + T2 * T2);
             if (rr > sa * T0) {
               if (sa * rr <= -T0) {
                 T0 = 0; T1 = 0; T2 = 0;
@@ -475,16 +480,16 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
                 T0 = tp; T1 *= sc; T2 *= sc;
               }
             }
-            const R nT = sqrt(T0 * T0 + T1 * T1 + T2 * T2);
+            const R nT = ::sqrt(T0 * T0 + T1 * T1 + T2 * T2);
             if (nT > tmax) { const R f = tmax / nT; T0 *= f; T1 *= f; T2 *= f; }
             if (valid && cc < 3) un = ((cc == 0 ? T0 : (cc == 1 ? T1 : T2)) - Tb) * ipT;
           }
           if (valid) {
-            du[o] = R(2) * un - uv;
+            du[o] = fma(R(2), un, -uv);
             ut[o] = uv + rho * (un - uv);
-            if (chk) {
+            if constexpr (chk) {
               const R old = uh[o];
-              zn = rmax(zn, fabs(un)); zo = rmax(zo, fabs(old)); zd = rmax(zd, fabs(un - old));
+              zn = umax(zn, OB::abs(un)); zo = umax(zo, OB::abs(old)); zd = umax(zd, OB::abs(un - old));
             }
             uh[o] = un;
           }
@@ -492,11 +497,11 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           // node 1: every component fixed by E_i
           const int i = q - PG;
           const R xv = xt[i], xn = zi[i];
-          dx[i] = R(2) * xn - xv;
+          dx[i] = fma(R(2), xn, -xv);
           xt[i] = xv + rho * (xn - xv);
-          if (chk) {
+          if constexpr (chk) {
             const R old = xh[i];
-            zn = rmax(zn, fabs(xn)); zo = rmax(zo, fabs(old)); zd = rmax(zd, fabs(xn - old));
+            zn = umax(zn, OB::abs(xn)); zo = umax(zo, OB::abs(old)); zd = umax(zd, OB::abs(xn - old));
           }
           xh[i] = xn;
         }
@@ -504,42 +509,38 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
     }
     __syncthreads();
     // ---- virtual controls and proportional-integral feedback (dual)
-    R rn = 0, ro = 0, rd = 0;
+    U rn = 0, ro = 0, rd = 0;
     for (int t = tid; t < PM + 32; t += T) {
       if (t < PM) {
         if (t < nm) {
           const int k = t / NX, i = t - NX * k;
           const R f = vph[t], a = nup[t], b = num[t];
-          const R mp = max0(a - alpha * (wep + f));
-          const R mm = max0(b - alpha * (wep - f));
-          nup[t] = a + rho * (mp - a);
-          num[t] = b + rho * (mm - b);
-          if (chk) {
+          const R mp = max0(a - alpha * f);
+          const R mm = max0(b + alpha * f);
+          nup[t] = omr * a + (rho * mp - raw);
+          num[t] = omr * b + (rho * mm - raw);
+          if constexpr (chk) {
             const R op = mup[t], om = mum[t];
-            zn = rmax(zn, rmax(mp, mm)); zo = rmax(zo, rmax(op, om));
-            zd = rmax(zd, rmax(fabs(mp - op), fabs(mm - om)));
+            zn = umax(zn, umax(OB::nonneg(mp), OB::nonneg(mm)));
+            zo = umax(zo, umax(OB::nonneg(op), OB::nonneg(om)));
+            zd = umax(zd, umax(OB::abs(mp - op), OB::abs(mm - om)));
           }
           mup[t] = mp;
           mum[t] = mm;
           const R* a_ = Am + (k * NX + i) * NX;
           const R* d = dx + k * NX;
-          R r = wv[t] + ((R(2) * mp - a) - (R(2) * mm - b)) - dx[(k + 1) * NX + i];
-          R r2 = 0;
+          R r = wv[t] + (fma(R(2), mp, -a) - fma(R(2), mm, -b)) - dx[(k + 1) * NX + i];
 #pragma unroll
-          for (int cc = 0; cc < NX; cc += 2) {
-            r += a_[cc] * d[cc];
-            if (cc + 1 < NX) r2 += a_[cc + 1] * d[cc + 1];
-          }
+          for (int cc = 0; cc < NX; ++cc) r += a_[cc] * d[cc];
           const R* bm = Bm + (k * NX + i) * NU;
           const R* bp = Bp + (k * NX + i) * NU;
 #pragma unroll
-          for (int cc = 0; cc < NU; ++cc) { r += bm[cc] * du[k * NU + cc]; r2 += bp[cc] * du[(k + 1) * NU + cc]; }
-          r += r2;
+          for (int cc = 0; cc < NU; ++cc) { r += bm[cc] * du[k * NU + cc]; r += bp[cc] * du[(k + 1) * NU + cc]; }
           const R pn = f + beta * r;
           vph[t] = f + rb * r;  // = f + rho (pn - f)
-          if (chk) {
+          if constexpr (chk) {
             const R old = phi[t];
-            rn = rmax(rn, fabs(pn)); ro = rmax(ro, fabs(old)); rd = rmax(rd, fabs(pn - old));
+            rn = umax(rn, OB::abs(pn)); ro = umax(ro, OB::abs(old)); rd = umax(rd, OB::abs(pn - old));
           }
           phi[t] = pn;
         }
@@ -550,20 +551,32 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           const R v = vth[k];
           const R tn = max0(v + beta * hy);
           vth[k] = v + rho * (tn - v);
-          if (chk) {
+          if constexpr (chk) {
             const R old = th[k];
-            rn = rmax(rn, tn); ro = rmax(ro, fabs(old)); rd = rmax(rd, fabs(tn - old));
+            rn = umax(rn, OB::nonneg(tn)); ro = umax(ro, OB::abs(old)); rd = umax(rd, OB::abs(tn - old));
           }
           th[k] = tn;
         }
       }
     }
-    if (chk) {
-      R v[6] = {zn, zo, zd, rn, ro, rd};
-      block_max_k<R, 6>(v, sm + L.red);
-      if (v[2] <= eabs + erel * rmax(v[0], v[1]) && v[5] <= eabs + erel * rmax(v[3], v[4])) break;
+    if constexpr (chk) {
+      U v[6] = {zn, zo, zd, rn, ro, rd};
+      block_max_u<U, 6>(v, reinterpret_cast<U*>(sm + L.red));
+      const R eabs = R(P.eps_abs), erel = R(P.eps_rel);
+      return OB::val(v[2]) <= eabs + erel * rmax(OB::val(v[0]), OB::val(v[1])) &&
+             OB::val(v[5]) <= eabs + erel * rmax(OB::val(v[3]), OB::val(v[4]));
     } else {
+      (void)zn; (void)zo; (void)zd; (void)rn; (void)ro; (void)rd;
       __syncthreads();
+      return false;
+    }
+  };
+  int j;
+  for (j = 1; j <= jmax; ++j) {
+    if (force <= 0 && jcheck > 0 && (j % jcheck) == 0) {
+      if (iterate(ChkTag<true>{})) break;
+    } else {
+      iterate(ChkTag<false>{});
     }
   }
   __syncthreads();
@@ -654,6 +667,8 @@ __device__ __forceinline__ R dot15_sm(const R (&a)[NX], const R* v, R g) {
 #endif
 template <typename R, int NU>
 __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /*image*/, R sigma, int force) {
+  using OB = OrdBits<R>;
+  using U = typename OB::U;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* const sm = reinterpret_cast<R*>(smraw);
   constexpr int G = NU <= 4 ? 4 : 8;
@@ -683,9 +698,18 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
   // registers.  Arrays: column of hat A^-_{kx} / row of hat A^-_{kd} / row of
   // hat B^-, hat B^+ (row thread); column of hat B^-_{ku} / of hat B^+_{ku-1}
   // (control thread).  Scalars by role:
-  //   row:     r0 x~, r1 x_hat, r2 nu+, r3 nu-, r4 mu+, r5 mu-, r6 phi~, r7 phi, r8 hat w
+  //   row:     r0 x~, r1 x_hat, r2 nu~+, r3 nu~-, r4 mu+, r5 mu-, r6 phi~, r7 phi, r8 hat w
+  //            (nu~ = nu - alpha w_ep, as in phase_pipg)
   //   control: r0 u~, r1 u_hat, r2 lo, r3 hi, r4 reference thrust,
   //            r5 theta~, r6 theta, r7 hat eps, r8 x~ node 1, r9 x_hat node 1, r10 hat z_i
+  const R wp = R(P.w_prox);
+  const R alpha = R(2) / (wp + sqrt(wp * wp + R(4) * R(P.omega) * sigma));
+  const R beta = R(P.omega) * alpha;
+  const R c1 = R(1) - alpha * wp;
+  const R rho = R(P.rho);
+  const R rb = rho * beta;
+  const R aw = alpha * R(P.w_ep);
+  const R omr = R(1) - rho, raw = rho * aw;
   R a1[NX], a2[NX], a3[2 * NU];
   R r0 = 0, r1 = 0, r2 = 0, r3 = 0, r4 = 0, r5 = 0, r6 = 0, r7 = 0, r8 = 0, r9 = 0, r10 = 0;
 #pragma unroll
@@ -706,8 +730,8 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
       a3[NU + c] = sm[L.Bp + (kd * NX + i) * NU + c];
     }
     r8 = sm[L.w + tid];
-    r4 = r2 = sm[L.mup + tid];
-    r5 = r3 = sm[L.mum + tid];
+    r4 = sm[L.mup + tid]; r2 = r4 - aw;
+    r5 = sm[L.mum + tid]; r3 = r5 - aw;
     r7 = r6 = sm[L.phi + tid];
     vp[kd * 16 + i] = r6;
   }
@@ -731,19 +755,11 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
   }
   if (has_x1) { r8 = r9 = sm[L.xh + v]; r10 = sm[L.zi + v]; }
   __syncthreads();
-  const R wp = R(P.w_prox);
-  const R alpha = R(2) / (wp + sqrt(wp * wp + R(4) * R(P.omega) * sigma));
-  const R beta = R(P.omega) * alpha;
-  const R c1 = R(1) - alpha * wp;
-  const R rho = R(P.rho);
-  const R rb = rho * beta;
-  const R wep = R(P.w_ep);
   const int jmax = force > 0 ? force : P.pipg_jmax;
   const int jcheck = P.pipg_jcheck;
-  int j;
-  for (j = 1; j <= jmax; ++j) {
-    const bool chk = force <= 0 && jcheck > 0 && (j % jcheck) == 0;
-    R zn = 0, zo = 0, zd = 0, rn = 0, ro = 0, rd = 0;
+  auto iterate = [&](auto chk_tag) -> bool {
+    constexpr bool chk = decltype(chk_tag)::value;
+    U zn = 0, zo = 0, zd = 0, rn = 0, ro = 0, rd = 0;
     // ---- projected gradient step (primal)
     if (has_d) {
       R G = -vp[kd * 16 + i];
@@ -755,9 +771,9 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
       if (last_x && i == IM) G -= R(P.w_cost);
       R xn = c1 * r0 - alpha * G;
       if (last_x && P.fix_f[i]) xn = sm[L.zf + i];
-      dxs[kx * 16 + i] = R(2) * xn - r0;
+      dxs[kx * 16 + i] = fma(R(2), xn, -r0);
       r0 += rho * (xn - r0);
-      if (chk) { zn = rmax(zn, fabs(xn)); zo = rmax(zo, fabs(r1)); zd = rmax(zd, fabs(xn - r1)); }
+      if constexpr (chk) { zn = umax(zn, OB::abs(xn)); zo = umax(zo, OB::abs(r1)); zd = umax(zd, OB::abs(xn - r1)); }
       r1 = xn;
     } else if (ctl) {
       R un = 0;
@@ -776,7 +792,7 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
         R T0 = __shfl_sync(0xffffffffu, tv, base);
         R T1 = __shfl_sync(0xffffffffu, tv, base + 1);
         R T2 = __shfl_sync(0xffffffffu, tv, base + 2);
-        const R rr = sqrt(T1 * T1 + T2 * T2);
+        const R rr = ::sqrt(T1 * T1 + T2 * T2);
         if (rr > sa * T0) {
           if (sa * rr <= -T0) {
             T0 = 0; T1 = 0; T2 = 0;
@@ -786,38 +802,38 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
             T0 = tp; T1 *= sc; T2 *= sc;
           }
         }
-        const R nT = sqrt(T0 * T0 + T1 * T1 + T2 * T2);
+        const R nT = ::sqrt(T0 * T0 + T1 * T1 + T2 * T2);
         if (nT > tmax) { const R q = tmax / nT; T0 *= q; T1 *= q; T2 *= q; }
         if (has_u && cc < 3) un = ((cc == 0 ? T0 : (cc == 1 ? T1 : T2)) - r4) * ipT;
       }
       if (has_u) {
-        dus[ku * NUP + cc] = R(2) * un - r0;
+        dus[ku * NUP + cc] = fma(R(2), un, -r0);
         r0 += rho * (un - r0);
-        if (chk) { zn = rmax(zn, fabs(un)); zo = rmax(zo, fabs(r1)); zd = rmax(zd, fabs(un - r1)); }
+        if constexpr (chk) { zn = umax(zn, OB::abs(un)); zo = umax(zo, OB::abs(r1)); zd = umax(zd, OB::abs(un - r1)); }
         r1 = un;
       }
       if (has_x1) {  // node 1: every component fixed by E_i
-        dxs[v] = R(2) * r10 - r8;
+        dxs[v] = fma(R(2), r10, -r8);
         r8 += rho * (r10 - r8);
-        if (chk) { zn = rmax(zn, fabs(r10)); zo = rmax(zo, fabs(r9)); zd = rmax(zd, fabs(r10 - r9)); }
+        if constexpr (chk) { zn = umax(zn, OB::abs(r10)); zo = umax(zo, OB::abs(r9)); zd = umax(zd, OB::abs(r10 - r9)); }
         r9 = r10;
       }
     }
     __syncthreads();
     // ---- virtual controls and proportional-integral feedback (dual)
     if (has_d) {
-      const R mp = max0(r2 - alpha * (wep + r6));
-      const R mm = max0(r3 - alpha * (wep - r6));
+      const R mp = max0(r2 - alpha * r6);
+      const R mm = max0(r3 + alpha * r6);
       const R a = r2, b = r3;
-      r2 = a + rho * (mp - a);
-      r3 = b + rho * (mm - b);
-      if (chk) {
-        zn = rmax(zn, rmax(mp, mm)); zo = rmax(zo, rmax(r4, r5));
-        zd = rmax(zd, rmax(fabs(mp - r4), fabs(mm - r5)));
+      r2 = omr * a + (rho * mp - raw);
+      r3 = omr * b + (rho * mm - raw);
+      if constexpr (chk) {
+        zn = umax(zn, umax(OB::nonneg(mp), OB::nonneg(mm))); zo = umax(zo, umax(OB::nonneg(r4), OB::nonneg(r5)));
+        zd = umax(zd, umax(OB::abs(mp - r4), OB::abs(mm - r5)));
       }
       r4 = mp;
       r5 = mm;
-      R r = r8 + ((R(2) * mp - a) - (R(2) * mm - b)) - dxs[kx * 16 + i];
+      R r = r8 + (fma(R(2), mp, -a) - fma(R(2), mm, -b)) - dxs[kx * 16 + i];
       r = dot15_sm(a2, dxs + kd * 16, r);
       R r2b = 0;
 #pragma unroll
@@ -833,25 +849,35 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
       r += r2b;
       const R pn = r6 + beta * r;
       r6 += rb * r;  // = phi~ + rho (phi_new - phi~)
-      if (chk) { rn = rmax(rn, fabs(pn)); ro = rmax(ro, fabs(r7)); rd = rmax(rd, fabs(pn - r7)); }
+      if constexpr (chk) { rn = umax(rn, OB::abs(pn)); ro = umax(ro, OB::abs(r7)); rd = umax(rd, OB::abs(pn - r7)); }
       r7 = pn;
       vp[kd * 16 + i] = r6;
     } else if (has_th) {
       const R hy = dxs[(v + 1) * 16 + IY] - dxs[v * 16 + IY] - r7;
       const R tn = max0(r5 + beta * hy);
       r5 += rho * (tn - r5);
-      if (chk) { rn = rmax(rn, tn); ro = rmax(ro, fabs(r6)); rd = rmax(rd, fabs(tn - r6)); }
+      if constexpr (chk) { rn = umax(rn, OB::nonneg(tn)); ro = umax(ro, OB::abs(r6)); rd = umax(rd, OB::abs(tn - r6)); }
       r6 = tn;
       vt[v] = r5;
     }
-    if (chk) {
-      R w6[6] = {zn, zo, zd, rn, ro, rd};
-      block_max_k<R, 6>(w6, sm + L.red);
-      if (w6[2] <= R(P.eps_abs) + R(P.eps_rel) * rmax(w6[0], w6[1]) &&
-          w6[5] <= R(P.eps_abs) + R(P.eps_rel) * rmax(w6[3], w6[4]))
-        break;
+    if constexpr (chk) {
+      U w6[6] = {zn, zo, zd, rn, ro, rd};
+      block_max_u<U, 6>(w6, reinterpret_cast<U*>(sm + L.red));
+      const R eabs = R(P.eps_abs), erel = R(P.eps_rel);
+      return OB::val(w6[2]) <= eabs + erel * rmax(OB::val(w6[0]), OB::val(w6[1])) &&
+             OB::val(w6[5]) <= eabs + erel * rmax(OB::val(w6[3]), OB::val(w6[4]));
     } else {
+      (void)zn; (void)zo; (void)zd; (void)rn; (void)ro; (void)rd;
       __syncthreads();
+      return false;
+    }
+  };
+  int j;
+  for (j = 1; j <= jmax; ++j) {
+    if (force <= 0 && jcheck > 0 && (j % jcheck) == 0) {
+      if (iterate(ChkTag<true>{})) break;
+    } else {
+      iterate(ChkTag<false>{});
     }
   }
   // iterates back to the image (warm start of the next SCP iteration)
