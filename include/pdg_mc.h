@@ -174,7 +174,7 @@ int pdg_mc_grad_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes
 int pdg_mc_launch_info(pdg_handle* h, int* threads, int* ctas_per_sm, int* smem_bytes);
 
 /* Override the threads-per-CTA of the solve kernels (multiple of 32 up to
- * 640, 0 = automatic).  Used by the autotuner.  The shared-memory PIPG form
+ * 576, 0 = automatic).  Used by the autotuner.  The shared-memory PIPG form
  * runs at most 512; the register form needs at least one thread per dual row
  * plus the control lanes (see pdg_mc_set_pipg_form); a solve whose setting
  * does not fit returns PDG_EINVAL. */
@@ -188,7 +188,7 @@ int pdg_mc_set_threads(pdg_handle* h, int threads);
  *           registers for the whole loop; only the vectors exchanged between
  *           the primal and dual steps go through shared memory.  Needs
  *           round32(15 (N-1)) + round32(N G) threads, G = 4 (nu = 4) or 8,
- *           at most 640 (FP32) or 512 (FP64);
+ *           at most 576 (FP32) or 512 (FP64);
  *   form 0: automatic (default) -- form 2 for FP32 when it fits, else form 1.
  * Returns PDG_EINVAL for another value.  Synchronous; no device work. */
 int pdg_mc_set_pipg_form(pdg_handle* h, int form);
@@ -225,6 +225,13 @@ int pdg_mc_solve_batch_noalloc(pdg_handle* h, int B, const double* x0, const int
  * and writes the best of three timed launches, in TFLOP/s, to *tflops.
  * Synchronizes the stream; allocates 16 bytes of device memory. */
 int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream);
+
+/* The same probe with only the first active_lanes (1..32) lanes of every warp
+ * running their chains; writes the best time in milliseconds to *ms.  The
+ * number of warp instructions does not depend on active_lanes, so equal times
+ * for 1 and 32 lanes show a pipe whose cost is per warp instruction (GB300's
+ * FP64 pipe).  PDG_EINVAL for other arguments.  Synchronizes the stream. */
+int pdg_mc_probe_fma_lanes(int precision, int active_lanes, double* ms, void* cuda_stream);
 
 #ifdef __cplusplus
 }

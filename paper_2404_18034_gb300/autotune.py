@@ -59,12 +59,12 @@ def reg_threads(n_max: int, nu: int) -> int:
 def candidates(n_max: int, nu: int, precision: int, forms: Iterable[int] = (1, 2)) -> Iterable[Tuple[int, int]]:
     """(form, CTA size) pairs with at least one discretization interval per
     wave whose shared-memory image fits on an SM (mirrors the kernel's layout
-    rule); the register form from its minimum up to 640 (FP32) or 512 threads."""
+    rule); the register form from its minimum up to 576 (FP32) or 512 threads."""
     out = []
     if 1 in forms:
         out += [(1, t) for t in _fitting(range(128, 513, 32), n_max, nu, precision)]
     if 2 in forms:
-        hi = 640 if precision == 1 else 512
+        hi = 576 if precision == 1 else 512
         out += [(2, t) for t in _fitting(range(reg_threads(n_max, nu), hi + 1, 32), n_max, nu, precision)]
     return out
 

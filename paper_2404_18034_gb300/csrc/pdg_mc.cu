@@ -28,12 +28,17 @@ using namespace pdg;
 #ifndef PDG_FP32_MIN_BLOCKS
 #define PDG_FP32_MIN_BLOCKS 3
 #endif
+// ... and the plain-form discretization kernel (its STM columns and model
+// evaluation want more registers than the other per-phase kernels)
+#ifndef PDG_FP32_DISC_MIN_BLOCKS
+#define PDG_FP32_DISC_MIN_BLOCKS 2
+#endif
 
 // PIPG forms: 1 = blocks in shared memory (phase_pipg), 2 = blocks and
 // iterates in registers (phase_pipg_reg).  The register form runs one thread
 // per dual row plus the control lanes, so its kernels are built for up to
 // PDG_REG_MAXT threads (FP32) or 512 (FP64).
-#define PDG_REG_MAXT_F32 544
+#define PDG_REG_MAXT_F32 576
 #define PDG_LB(R, PV)                                                                       \
   __launch_bounds__((PV) == 2 && sizeof(R) == 4 ? PDG_REG_MAXT_F32 : 512,                   \
                     sizeof(R) == 4 && (PV) != 2 ? PDG_FP32_MIN_BLOCKS : 1)
@@ -257,7 +262,7 @@ k_plain_init(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
 }
 
 template <typename R, int NU>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_DISC_MIN_BLOCKS : 1)
 k_plain_disc(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W) {
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -568,8 +573,10 @@ __global__ void k_class_sort(int B, const int* __restrict__ Ns, int n_max, int* 
 
 // FMA-chain probe for the roofline denominator: every thread runs 8
 // independent dependency chains of `iters` FMAs each (16 flops per step).
+// Lanes >= active of every warp return at once (active = 32: all work).
 template <typename R>
-__global__ void k_fma_probe(int iters, R seed, R* out) {
+__global__ void k_fma_probe(int iters, int active, R seed, R* out) {
+  if ((threadIdx.x & 31) >= active) return;
   R a0 = seed + R(threadIdx.x), a1 = a0 + R(1), a2 = a0 + R(2), a3 = a0 + R(3);
   R a4 = a0 + R(4), a5 = a0 + R(5), a6 = a0 + R(6), a7 = a0 + R(7);
   const R m = R(0.999999), c = R(1e-7);
@@ -1315,7 +1322,7 @@ int pdg_mc_pipg_form(const pdg_handle* h) { return h ? h->last_variant : PDG_EIN
 int pdg_mc_set_threads(pdg_handle* h, int threads) {
   if (!h) return PDG_EINVAL;
   if (threads < 0 || threads > PDG_REG_MAXT_F32 || (threads % 32) != 0)
-    return fail(h, PDG_EINVAL, "threads must be 0 or a multiple of 32 up to 640");
+    return fail(h, PDG_EINVAL, "threads must be 0 or a multiple of 32 up to " + std::to_string(PDG_REG_MAXT_F32));
   h->threads_override = threads;
   return PDG_OK;
 }
@@ -1349,8 +1356,7 @@ int pdg_mc_grad_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes
                       : run_grad<7>(h, B, x0, n_nodes, dL_dfuel, dL_dtouch, grad_x0, fuel, touch, status, s);
 }
 
-int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream) {
-  if (!tflops || (precision != 0 && precision != 1)) return PDG_EINVAL;
+static int probe_fma_run(int precision, int active, double* best_ms, long long* lane_fma, void* cuda_stream) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return PDG_ECUDA;
@@ -1365,8 +1371,8 @@ int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream) {
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(e0, s);
-    if (precision == 0) k_fma_probe<double><<<blocks, threads, 0, s>>>(iters, 1.0, (double*)buf);
-    else k_fma_probe<float><<<blocks, threads, 0, s>>>(iters, 1.0f, (float*)buf);
+    if (precision == 0) k_fma_probe<double><<<blocks, threads, 0, s>>>(iters, active, 1.0, (double*)buf);
+    else k_fma_probe<float><<<blocks, threads, 0, s>>>(iters, active, 1.0f, (float*)buf);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
     float ms = 0;
@@ -1378,8 +1384,24 @@ int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream) {
   cudaEventDestroy(e1);
   cudaFree(buf);
   if (e != cudaSuccess) return PDG_ECUDA;
-  *tflops = 16.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+  *best_ms = best;
+  *lane_fma = 8LL * iters * blocks * threads;
   return PDG_OK;
+}
+
+int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream) {
+  if (!tflops || (precision != 0 && precision != 1)) return PDG_EINVAL;
+  double ms = 0;
+  long long n = 0;
+  if (int rc = probe_fma_run(precision, 32, &ms, &n, cuda_stream)) return rc;
+  *tflops = 2.0 * (double)n / (ms * 1e-3) / 1e12;
+  return PDG_OK;
+}
+
+int pdg_mc_probe_fma_lanes(int precision, int active_lanes, double* ms, void* cuda_stream) {
+  if (!ms || (precision != 0 && precision != 1) || active_lanes < 1 || active_lanes > 32) return PDG_EINVAL;
+  long long n = 0;
+  return probe_fma_run(precision, active_lanes, ms, &n, cuda_stream);
 }
 
 }  // extern "C"

@@ -23,7 +23,7 @@ ERRORS = {-1: "PDG_EINVAL", -2: "PDG_ENOMEM", -3: "PDG_ECUDA"}
 EXPORTS = ("pdg_mc_init", "pdg_mc_destroy", "pdg_mc_last_error", "pdg_mc_solve_batch",
            "pdg_mc_solve_batch_host", "pdg_mc_subproblem", "pdg_mc_scp_step", "pdg_mc_launch_info",
            "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc",
-           "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form")
+           "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form", "pdg_mc_probe_fma_lanes")
 
 
 class PdgParams(C.Structure):
@@ -76,10 +76,12 @@ def load_library(path: str = LIB_PATH):
     L.pdg_mc_solve_batch_noalloc.argtypes = [_VP, C.c_int, _VP, _VP] + [_VP] * 7 + [_VP]
     L.pdg_mc_grad_batch.argtypes = [_VP, C.c_int] + [_VP] * 8 + [_VP]
     L.pdg_mc_set_pipg_form.argtypes = [_VP, C.c_int]
+    L.pdg_mc_probe_fma_lanes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), _VP]
     L.pdg_mc_pipg_form.argtypes = [_VP]
     for name in ("pdg_mc_init", "pdg_mc_solve_batch", "pdg_mc_solve_batch_host", "pdg_mc_subproblem",
                  "pdg_mc_scp_step", "pdg_mc_launch_info", "pdg_mc_set_threads", "pdg_mc_probe_fma",
-                 "pdg_mc_solve_batch_noalloc", "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form"):
+                 "pdg_mc_solve_batch_noalloc", "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form",
+                 "pdg_mc_probe_fma_lanes"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -125,6 +127,23 @@ def probe_fma(precision: int = 0, stream=None) -> float:
     if rc != 0:
         raise RuntimeError(f"pdg_mc_probe_fma: {ERRORS.get(rc, rc)}")
     return out.value
+
+
+def probe_fma_lanes(precision: int = 0, lanes=(32, 16, 8, 1), stream=None) -> Dict[int, float]:
+    """Best time (ms) of the FMA-chain probe with only `k` active lanes per
+    warp, for each k in lanes (pdg_mc_probe_fma_lanes).  The warp-instruction
+    count is the same for every k."""
+    import torch
+    L = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    res = {}
+    for k in lanes:
+        out = C.c_double()
+        rc = L.pdg_mc_probe_fma_lanes(int(precision), int(k), C.byref(out), C.c_void_p(s.cuda_stream))
+        if rc != 0:
+            raise RuntimeError(f"pdg_mc_probe_fma_lanes: {ERRORS.get(rc, rc)}")
+        res[int(k)] = out.value
+    return res
 
 
 class Solver:
