@@ -161,18 +161,24 @@ int orc_g(const orc_params* p, const double* x, const double* u, double* g) {
   g[6] = nT - p->T_max;
   if (p->soc_thrust) { g[5] = -1.0; g[6] = -1.0; }  /* imposed by projection instead */
   g[7] = p->T_min - nT;
+  int ng = 8;
   if (p->nu == 7) {
     const double* gm = u + 3;
-    g[8] = dot3(gm, gm) - p->gamma_max * p->gamma_max;
-    return 9;
+    g[ng++] = dot3(gm, gm) - p->gamma_max * p->gamma_max;
   }
-  return 8;
+  /* glide slope (parameter gamma_gs of Sec. 5; its row is not printed): the
+     vehicle stays in the cone tan(gamma_gs) ||(r_y, r_z)|| <= r_x about the
+     inertial up axis through the landing site.  Written squared,
+     tan^2 (r_y^2 + r_z^2) - r_x^2 <= 0, which with the altitude row r_x >= 0
+     is the same cone and is smooth at its apex (the touchdown point). */
+  if (p->glide_slope) g[ng++] = p->tan_gs * p->tan_gs * (r[1] * r[1] + r[2] * r[2]) - r[0] * r[0];
+  return ng;
 }
 
 /* f(x, u) = s (F, 1^T |g|_+^2), Eq. sys-dyn-dil-aug (no h in this problem). */
 void orc_f(const orc_params* p, const double* x, const double* u, double* f) {
   double s = u[p->nu - 1];
-  double Fx[14], g[9];
+  double Fx[14], g[10];
   orc_F(p, x, u, Fx);
   int ng = orc_g(p, x, u, g);
   double pen = 0;
@@ -197,10 +203,10 @@ void orc_jac(const orc_params* p, const double* x, const double* u, double* A, d
   memset(B, 0, sizeof(double) * NX * nu);
 #define AA(i, j) A[(i) * NX + (j)]
 #define BB(i, j) B[(i) * nu + (j)]
-  double Fx[14], g[9];
+  double Fx[14], g[10];
   orc_F(p, x, u, Fx);
   int ng = orc_g(p, x, u, g);
-  double gp[9];
+  double gp[10];
   double pen = 0;
   for (int i = 0; i < ng; i++) {
     gp[i] = g[i] > 0 ? g[i] : 0;
@@ -247,6 +253,12 @@ void orc_jac(const orc_params* p, const double* x, const double* u, double* A, d
   AA(XY, XQ + 2) += s * 2.0 * gp[3] * (4.0 * q[2]);
   AA(XY, XQ + 3) += s * 2.0 * gp[3] * (4.0 * q[3]);
   for (int i = 0; i < 3; i++) AA(XY, XW + i) += s * 2.0 * gp[4] * (2.0 * w[i]);
+  if (p->glide_slope) {  /* the glide-slope row is the last one */
+    const double ggs = gp[ng - 1], t2 = p->tan_gs * p->tan_gs;
+    AA(XY, XR + 0) += s * 2.0 * ggs * (-2.0 * x[XR + 0]);
+    AA(XY, XR + 1) += s * 2.0 * ggs * (2.0 * t2 * x[XR + 1]);
+    AA(XY, XR + 2) += s * 2.0 * ggs * (2.0 * t2 * x[XR + 2]);
+  }
 
   /* --- d/dT --- */
   for (int j = 0; j < 3; j++) BB(XM, j) = s * (-p->alpha_mdot * Tu[j]);
@@ -435,12 +447,20 @@ void orc_scale(const orc_params* p, int N, const double* x0, const double* X, co
     /* hat eps_k = eps E_y P_x^{-1} E_y^T - E_y P_x^{-1} (xbar_{k+1} - xbar_k) */
     qp->eps[k] = p->eps_ctcs / Px[XY] - (X[(k + 1) * NX + XY] - X[k * NX + XY]) / Px[XY];
   }
-  /* control box on the dilation factor only (Sec. 5, R6) */
+  /* control box on the dilation factor only (Sec. 5, R6).  The time bounds
+     of Sec. 2.2 tighten it node-wise: with FOH s, Delta t_k = (s_k + s_{k+1})
+     / (2 (N-1)) lies between the node values / (N-1), and t_f = sum Delta t_k
+     is at most max_k s_k, so s_k in [dt_min (N-1), min(dt_max (N-1), tf_max)]
+     is sufficient for dt_min <= Delta t_k <= dt_max and t_f <= tf_max. */
+  double smin = p->s_min, smax = p->s_max;
+  if (p->dt_min > 0 && p->dt_min * (N - 1) > smin) smin = p->dt_min * (N - 1);
+  if (p->dt_max > 0 && p->dt_max * (N - 1) < smax) smax = p->dt_max * (N - 1);
+  if (p->tf_max > 0 && p->tf_max < smax) smax = p->tf_max;
   for (int k = 0; k < N; k++) {
     for (int c = 0; c < nu; c++) {
       if (c == nu - 1) {
-        qp->umin[k * nu + c] = (p->s_min - U[k * nu + c]) / Pu[c];
-        qp->umax[k * nu + c] = (p->s_max - U[k * nu + c]) / Pu[c];
+        qp->umin[k * nu + c] = (smin - U[k * nu + c]) / Pu[c];
+        qp->umax[k * nu + c] = (smax - U[k * nu + c]) / Pu[c];
       } else {
         qp->umin[k * nu + c] = -INFINITY;
         qp->umax[k * nu + c] = INFINITY;

@@ -49,6 +49,9 @@ typedef struct orc_params {
   double tf_guess;        /* initial guess of the final time */
   int soc_thrust;         /* 1: T_max and gimbal bounds as a per-node second-order-cone
                              projection in PIPG instead of CTCS rows */
+  int glide_slope;        /* 1: glide-slope row tan(gamma_gs) ||(r_y, r_z)|| - r_x <= 0 in g */
+  double tan_gs;          /* tan(gamma_gs), gamma_gs measured from the horizontal */
+  double dt_min, dt_max, tf_max;  /* Sec. 2.2 time bounds; 0 = off (node box on s) */
 } orc_params;
 
 /* Scaled convex subproblem data (Eq. cvx-subproblem-custom). */

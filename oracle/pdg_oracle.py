@@ -9,6 +9,7 @@ dict and the initial conditions produced by ``paper_2404_18034_gb300.inputs``.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -60,6 +61,8 @@ class Params(C.Structure):
         ("rk4_substeps", C.c_int),
         ("tf_guess", C.c_double),
         ("soc_thrust", C.c_int),
+        ("glide_slope", C.c_int), ("tan_gs", C.c_double),
+        ("dt_min", C.c_double), ("dt_max", C.c_double), ("tf_max", C.c_double),
     ]
 
 
@@ -155,6 +158,10 @@ def make_params(p: Dict) -> Params:
     for i in range(15):
         s.fix_f[i] = int(p["fix_f"][i])
     s.soc_thrust = int(p.get("soc_thrust", 0))
+    s.glide_slope = int(p.get("glide_slope", 0))
+    s.tan_gs = math.tan(float(p.get("gamma_gs", 0.0)))
+    for k in ("dt_min", "dt_max", "tf_max"):
+        setattr(s, k, float(p.get(k, 0.0)))
     return s
 
 
@@ -170,7 +177,7 @@ def F(p, x, u):
 
 
 def g(p, x, u):
-    out = np.zeros(9)
+    out = np.zeros(10)
     n = lib().orc_g(C.byref(make_params(p)), _d(np.ascontiguousarray(x, np.float64)),
                     _d(np.ascontiguousarray(u, np.float64)), _d(out))
     return out[:n]

@@ -62,11 +62,18 @@ def load_params(path: Optional[str] = None, nu: Optional[int] = None, **override
     for k in ("pipg_jmax", "pipg_jcheck", "pow_jmax", "scp_jmax", "rk4_substeps"):
         p[k] = int(raw[k])
     p["soc_thrust"] = int(raw.get("soc_thrust", 0))
+    # glide slope (gamma_gs of Sec. 5, from the horizontal) and the Sec. 2.2
+    # time bounds (0 = off); off in the default workloads
+    p["glide_slope"] = int(raw.get("glide_slope", 0))
+    p["dt_min"] = float(raw.get("dt_min", 0.0))
+    p["dt_max"] = float(raw.get("dt_max", 0.0))
+    p["tf_max"] = float(raw.get("tf_max", 0.0))
     for k in ("g_I", "J_B", "r_T_B"):
         p[k] = np.asarray(raw[k], dtype=np.float64)
     p["theta_max"] = raw["theta_max_deg"] * d2r
     p["omega_max"] = raw["omega_max_deg"] * d2r
     p["delta_max"] = raw["delta_max_deg"] * d2r
+    p["gamma_gs"] = float(raw.get("gamma_gs_deg", 30.0)) * d2r
     zf = np.zeros(NX)
     zf[1:4] = raw["r_f"]
     zf[4:7] = raw["v_f"]
