@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--grad", action="store_true", help="time gradients (pdg_mc_grad_batch) instead of solves")
     ap.add_argument("--soc", action="store_true",
                     help="thrust magnitude and gimbal bounds as a second-order-cone projection in PIPG")
+    ap.add_argument("--glide-slope", action="store_true", help="add the glide-slope CTCS row (gamma_gs)")
+    ap.add_argument("--dt-min", type=float, default=0.0, help="Delta t_k lower bound (0: off)")
+    ap.add_argument("--dt-max", type=float, default=0.0, help="Delta t_k upper bound (0: off)")
+    ap.add_argument("--tf-max", type=float, default=0.0, help="final-time bound (0: off)")
     ap.add_argument("--pipg-form", type=int, default=0, choices=[0, 1, 2],
                     help="PIPG layout: 0 autotune cache / automatic, 1 shared memory, 2 registers")
     ap.add_argument("--err-sample", type=int, default=512,
@@ -98,7 +102,9 @@ def workload_name(a):
     n = "Nuneven10-30" if a.uneven else f"N{a.nodes}"
     nu = "" if a.nu == 4 else f"_nu{a.nu}"
     soc = "_soc" if getattr(a, "soc", False) else ""
-    return f"pdg6dof_{a.dispersion}_B{a.batch}_{n}{nu}{soc}_{a.precision}_{a.mode}"
+    gs = "_gs" if getattr(a, "glide_slope", False) else ""
+    tb = "_tbounds" if (getattr(a, "dt_min", 0) or getattr(a, "dt_max", 0) or getattr(a, "tf_max", 0)) else ""
+    return f"pdg6dof_{a.dispersion}_B{a.batch}_{n}{nu}{soc}{gs}{tb}_{a.precision}_{a.mode}"
 
 
 class ClockSampler:
@@ -303,7 +309,8 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     prec = 0 if a.precision == "fp64" else 1
-    p = inputs.load_params(nu=a.nu, soc_thrust=int(a.soc))
+    p = inputs.load_params(nu=a.nu, soc_thrust=int(a.soc), glide_slope=int(a.glide_slope), dt_min=a.dt_min,
+                           dt_max=a.dt_max, tf_max=a.tf_max)
     seed = shard_seed(inputs.config_seed(2), rank)
     x0h = inputs.dispersion(p, a.batch, seed, a.dispersion)
     x0 = torch.from_numpy(x0h).to(dev)

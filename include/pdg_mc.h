@@ -74,6 +74,12 @@ typedef struct pdg_params {
                              inside PIPG (second-order cone then ball, Alg. 1's
                              projection step) instead of CTCS rows; needs P_u equal on
                              the three thrust components; no gradients */
+  int glide_slope;        /* 1: add the glide-slope row tan^2(gamma_gs) (r_y^2 + r_z^2) - r_x^2
+                             <= 0 to g (CTCS), the bound gamma_gs named in Sec. 5 */
+  double gamma_gs;        /* glide-slope angle from the horizontal (rad), in (0, pi/2) */
+  double dt_min, dt_max, tf_max;  /* Sec. 2.2 time bounds, 0 = off: imposed as the node box
+                             s_k in [dt_min (N-1), min(dt_max (N-1), tf_max)] on the
+                             dilation (sufficient for FOH s) */
 } pdg_params;
 
 typedef struct pdg_handle pdg_handle;

@@ -79,7 +79,7 @@ def _fitting(ts: Iterable[int], n_max: int, nu: int, precision: int) -> Iterable
         n = n_max
         img = 8 + 16 + n * NX + n * nu + (n - 1) * (NX * NX + 2 * NX * nu + NX + 1) + 2 * n + 2 * NX + \
             n * NX + n * nu + 3 * (n - 1) * NX + (n - 1)
-        uni = max(2 * n * NX + 2 * n * nu + 4 * (n - 1) * NX + (n - 1), ipw * (40 + NX * nu + 3 * NX))
+        uni = max(2 * n * NX + 2 * n * nu + 4 * (n - 1) * NX + (n - 1), ipw * (42 + NX * nu + 3 * NX))
         if (img + uni + 210) * esz > SMEM_MAX:
             continue
         yield t

@@ -69,7 +69,7 @@ __device__ __forceinline__ void model_vjp(const double* A, const double* Bd, con
   xb[12] += A[23] * v[11]; xb[13] += A[24] * v[11];
   xb[11] += A[25] * v[12]; xb[13] += A[26] * v[12];
   xb[11] += A[27] * v[13]; xb[12] += A[28] * v[13];
-  xb[0] += A[29] * v[14]; xb[1] += A[30] * v[14];
+  xb[0] += A[29] * v[14]; xb[1] += A[30] * v[14]; xb[2] += A[39] * v[14]; xb[3] += A[40] * v[14];
   xb[4] += A[31] * v[14]; xb[5] += A[32] * v[14]; xb[6] += A[33] * v[14];
   xb[9] += A[34] * v[14]; xb[10] += A[35] * v[14];
   xb[11] += A[36] * v[14]; xb[12] += A[37] * v[14]; xb[13] += A[38] * v[14];

@@ -31,6 +31,10 @@ struct DParams {
   double budget_ns;  // 0 = none
   int soc;           // thrust sector by projection (T_max, gimbal rows off)
   double soc_tan;    // tan(delta_max)
+  int gs;            // glide-slope row on
+  double tan_gs2;    // tan^2(gamma_gs)
+  double s_lo, s_hi; // node box on the dilation: [s_min, s_max] tightened by the time bounds,
+  double dt_lo, dt_hi;  // of which dt_min, dt_max scale with N - 1 (0 = off)
 };
 
 // Per-instance shared-memory layout (element offsets in units of R).  The
@@ -44,7 +48,7 @@ struct Lay {
 
 // stage buffer of one interval: compact A (40), dense B (15 x nu), then the
 // evaluator's RK4 state of x: base P, accumulator, stage input (15 each)
-constexpr int SA_A = 40;
+constexpr int SA_A = 42;
 
 // Intervals per discretization wave: warp 0 evaluates the model of up to 32
 // intervals, the remaining warps hold one STM column per thread.
@@ -204,6 +208,7 @@ __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
 //   [19..22] (s/2) q  -> q rows wrt w through Xi(q)
 //   [23..28] dwdot/dw off-diagonals (01, 02, 10, 12, 20, 21)
 //   [29..38] y row: m, r_x, v0..2, q2, q3, w0..2
+//   [39..40] y row: r_y, r_z (glide slope); [41] unused
 // ---------------------------------------------------------------------------
 template <typename R, int NU>
 __device__ __forceinline__ void model_eval(const DParams& P, const R* x, const R* u, R* f, R* A, R* Bd) {
@@ -245,7 +250,7 @@ __device__ __forceinline__ void model_eval(const DParams& P, const R* x, const R
   F[10] = R(0.5) * (w2 * q0 + w1 * q1 - w0 * q2);
   F[11] = tq0 * iJ0; F[12] = tq1 * iJ1; F[13] = tq2 * iJ2;
   // path constraints (tilt row per the reading 2(q2^2+q3^2) - (1 - cos theta_max))
-  R gp[9];
+  R gp[10];
   gp[0] = R(P.m_dry) - m;
   gp[1] = -x[IR];
   gp[2] = v0 * v0 + v1 * v1 + v2 * v2 - R(P.vmax2);
@@ -256,9 +261,12 @@ __device__ __forceinline__ void model_eval(const DParams& P, const R* x, const R
   gp[7] = R(P.T_min) - nT;
   gp[8] = (NU == 7) ? (gm0 * gm0 + gm1 * gm1 + gm2 * gm2 - R(P.gamma_max2)) : R(-1);
   if (P.soc) { gp[5] = R(-1); gp[6] = R(-1); }  // imposed by projection instead
+  // glide slope, squared so that it is smooth at the cone's apex (touchdown)
+  const R rx = x[IR], ry = x[IR + 1], rz = x[IR + 2];
+  gp[9] = P.gs ? R(P.tan_gs2) * (ry * ry + rz * rz) - rx * rx : R(-1);
   R pen = 0;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
+  for (int i = 0; i < 10; ++i) {
     gp[i] = gp[i] > R(0) ? gp[i] : R(0);
     pen += gp[i] * gp[i];
   }
@@ -292,7 +300,7 @@ __device__ __forceinline__ void model_eval(const DParams& P, const R* x, const R
   A[28] = -s * iJ2 * (J1 - J0) * w0;
   const R s2 = R(2) * s;
   A[29] = -s2 * gp[0];
-  A[30] = -s2 * gp[1];
+  A[30] = -s2 * (gp[1] + gp[9] * R(2) * rx);
   A[31] = s2 * gp[2] * R(2) * v0;
   A[32] = s2 * gp[2] * R(2) * v1;
   A[33] = s2 * gp[2] * R(2) * v2;
@@ -301,7 +309,9 @@ __device__ __forceinline__ void model_eval(const DParams& P, const R* x, const R
   A[36] = s2 * gp[4] * R(2) * w0;
   A[37] = s2 * gp[4] * R(2) * w1;
   A[38] = s2 * gp[4] * R(2) * w2;
-  A[39] = 0;
+  A[39] = s2 * gp[9] * R(2) * R(P.tan_gs2) * ry;
+  A[40] = s2 * gp[9] * R(2) * R(P.tan_gs2) * rz;
+  A[41] = 0;
   // dense df/du
 #pragma unroll
   for (int i = 0; i < NX * NU; ++i) Bd[i] = R(0);
@@ -348,7 +358,7 @@ __device__ __forceinline__ void model_jvp(const R* __restrict__ A, const R* __re
   d[12] = A[25] * b0 + A[26] * b2;
   d[13] = A[27] * b0 + A[28] * b1;
   d[14] = A[29] * S[0] + A[30] * S[1] + A[31] * S[4] + A[32] * S[5] + A[33] * S[6] + A[34] * a2 + A[35] * a3 +
-          A[36] * b0 + A[37] * b1 + A[38] * b2;
+          A[36] * b0 + A[37] * b1 + A[38] * b2 + A[39] * S[2] + A[40] * S[3];
   if (cu >= 0) {
 #pragma unroll
     for (int i = 0; i < NX; ++i) d[i] += lam * Bd[i * NU + cu];

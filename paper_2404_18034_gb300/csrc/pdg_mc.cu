@@ -713,6 +713,16 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
   d->tf_guess = p->tf_guess;
   d->g0 = sqrt(p->g_I[0] * p->g_I[0] + p->g_I[1] * p->g_I[1] + p->g_I[2] * p->g_I[2]);
   d->budget_ns = p->budget_seconds > 0 ? p->budget_seconds * 1e9 : 0.0;
+  d->gs = p->glide_slope ? 1 : 0;
+  if (d->gs && !(p->gamma_gs > 0 && p->gamma_gs < 1.5707963267948966)) {
+    *why = "gamma_gs must lie in (0, pi/2) with glide_slope on"; return false;
+  }
+  d->tan_gs2 = d->gs ? tan(p->gamma_gs) * tan(p->gamma_gs) : 0.0;
+  if (p->dt_min < 0 || p->dt_max < 0 || p->tf_max < 0) { *why = "dt_min, dt_max, tf_max must be >= 0 (0 = off)"; return false; }
+  d->s_lo = p->s_min;
+  d->s_hi = p->tf_max > 0 && p->tf_max < p->s_max ? p->tf_max : p->s_max;
+  d->dt_lo = p->dt_min;
+  d->dt_hi = p->dt_max;
   d->soc = p->soc_thrust ? 1 : 0;
   d->soc_tan = tan(p->delta_max);
   if (d->soc && !(p->P_u[0] == p->P_u[1] && p->P_u[1] == p->P_u[2])) {

@@ -192,10 +192,14 @@ __device__ void phase_scale_extra(const DParams& P, const Lay& L, R* sm) {
     if (t < N - 1) {
       sm[L.eps + t] = R(P.eps_ctcs) * iPy - (Xb[(t + 1) * NX + IY] - Xb[t * NX + IY]) * iPy;
     } else if (t < 2 * N - 1) {
+      // dilation box; the Sec. 2.2 time bounds tighten it (sufficient node box for FOH s)
       const int k = t - (N - 1);
       const R s = Ub[k * NU + NU - 1];
-      sm[L.lo + k] = (R(P.s_min) - s) * iPs;
-      sm[L.hi + k] = (R(P.s_max) - s) * iPs;
+      double lo = P.s_lo, hi = P.s_hi;
+      if (P.dt_lo > 0.0 && P.dt_lo * (N - 1) > lo) lo = P.dt_lo * (N - 1);
+      if (P.dt_hi > 0.0 && P.dt_hi * (N - 1) < hi) hi = P.dt_hi * (N - 1);
+      sm[L.lo + k] = (R(lo) - s) * iPs;
+      sm[L.hi + k] = (R(hi) - s) * iPs;
     } else {
       const int i = t - (2 * N - 1);
       sm[L.zi + i] = (x0[i] - Xb[i]) * R(P.Pxinv[i]);

@@ -46,6 +46,8 @@ class PdgParams(C.Structure):
         ("rk4_substeps", C.c_int),
         ("tf_guess", C.c_double), ("budget_seconds", C.c_double),
         ("soc_thrust", C.c_int),
+        ("glide_slope", C.c_int), ("gamma_gs", C.c_double),
+        ("dt_min", C.c_double), ("dt_max", C.c_double), ("tf_max", C.c_double),
     ]
 
 
@@ -106,6 +108,10 @@ def make_params(p: Dict, precision: int = 0, budget_seconds: float = 0.0) -> Pdg
         s.fix_f[i] = int(p["fix_f"][i])
     s.budget_seconds = float(budget_seconds)
     s.soc_thrust = int(p.get("soc_thrust", 0))
+    s.glide_slope = int(p.get("glide_slope", 0))
+    s.gamma_gs = float(p.get("gamma_gs", 0.0))
+    for k in ("dt_min", "dt_max", "tf_max"):
+        setattr(s, k, float(p.get(k, 0.0)))
     return s
 
 

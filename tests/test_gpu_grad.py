@@ -27,11 +27,12 @@ def _fd(oracle, p, x0, X, U, ws, sig, n, h=1e-6):
     return g
 
 
-@pytest.mark.parametrize("nu,N,B", [(4, 15, 6), (4, 10, 3), (7, 12, 2)])
-def test_gradient_matches_oracle_finite_differences(torch_cuda, oracle, inputs, nu, N, B):
+@pytest.mark.parametrize("nu,N,B,ov", [(4, 15, 6, {}), (4, 10, 3, {}), (7, 12, 2, {}),
+                                        (4, 12, 3, {"glide_slope": 1, "dt_min": 0.3, "dt_max": 0.55})])
+def test_gradient_matches_oracle_finite_differences(torch_cuda, oracle, inputs, nu, N, B, ov):
     torch = torch_cuda
     from paper_2404_18034_gb300.pdg_mc import Solver
-    p = inputs.load_params(nu=nu)
+    p = inputs.load_params(nu=nu, **ov)
     S = Solver(p, N)
     x0 = inputs.dispersion(p, B, inputs.config_seed(3), "bj")
     d = torch.from_numpy(x0).cuda()
