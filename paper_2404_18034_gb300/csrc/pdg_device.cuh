@@ -43,7 +43,7 @@ struct DParams {
 struct Lay {
   int N, nu, ipw, sa;
   int sc, x0, Xb, Ub, Am, Bm, Bp, w, eps, lo, hi, zi, zf, xh, uh, mup, mum, phi, th, img;
-  int xt, ut, nup, num, vph, vth, dx, du, dmu, stage, red, total;
+  int xt, ut, nup, num, vph, vth, dx, du, td, stage, red, total;
 };
 
 // stage buffer of one interval: compact A (40), dense B (15 x nu), then the
@@ -97,7 +97,7 @@ __host__ __device__ inline Lay make_lay(int N, int nu, int threads) {
   L.vth = u; u += N - 1;
   L.dx = u; u += N * NX;
   L.du = u; u += N * nu;
-  L.dmu = u; u += (N - 1) * NX;
+  L.td = u; u += (N - 1) * NX;  // PIPG: CTCS-dual difference per node (N used)
   int u2 = o;
   L.stage = u2; u2 += L.ipw * L.sa;
   o = u > u2 ? u : u2;

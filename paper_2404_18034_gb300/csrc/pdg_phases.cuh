@@ -383,6 +383,10 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
   R* vth = sm + L.vth;
   R* dx = sm + L.dx;
   R* du = sm + L.du;
+  // td[k] = theta~_{k-1} - theta~_k (k < N-1) or theta~_{N-2} (k = N-1): the
+  // CTCS rows' contribution to the y component of node k's gradient, formed
+  // by the CTCS warp so that the x step carries no per-component branch
+  R* td = sm + L.td;
   const R wp = R(P.w_prox);
   const R alpha = R(2) / (wp + sqrt(wp * wp + R(4) * R(P.omega) * sigma));
   const R beta = R(P.omega) * alpha;
@@ -403,6 +407,7 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
     else if (t < N * NX + N * NU + 2 * nm) { const int q = t - N * NX - N * NU - nm; vph[q] = phi[q]; }
     else { const int q = t - N * NX - N * NU - 2 * nm; vth[q] = th[q]; }
   }
+  for (int k = 1 + tid; k < N; k += T) td[k] = th[k - 1] - (k < N - 1 ? th[k] : R(0));
   __syncthreads();
   const R sa = R(P.soc_tan), tmax = R(P.T_max), pT = R(P.Pu[0]), ipT = R(P.Puinv[0]);
   const int jmax = force > 0 ? force : P.pipg_jmax;
@@ -416,21 +421,24 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
     for (int t = tid; t < PX + PU; t += T) {
       if (t < PX) {
         if (t < nxk) {
+          // branch-free: on GB300 a divergent FP64 instruction costs a full
+          // warp slot, and per-component special cases split the warp
           const int k = t / NX + 1, i = t - NX * (k - 1);
           const int o = k * NX + i;
+          const bool last = k == N - 1;
+          const int km = last ? 0 : k;  // the last node has no A block: any valid one, result discarded
           const R xv = xt[o];
-          R G = -vph[(k - 1) * NX + i];
-          if (k < N - 1) {
-            const R* a = Am + k * NX * NX + i;
-            const R* f = vph + k * NX;
+          const R G0 = fma(i == IY ? R(1) : R(0), td[k], -vph[(k - 1) * NX + i]);
+          R Gc = G0;
+          const R* a = Am + km * NX * NX + i;
+          const R* f = vph + km * NX;
 #pragma unroll
-            for (int r = 0; r < NX; ++r) G += a[r * NX] * f[r];
-            if (i == IY) G -= vth[k];
-          }
-          if (i == IY) G += vth[k - 1];
-          if (k == N - 1 && i == IM) G -= wcost;  // e_cost = -e_m (maximize m_N)
-          R xn = c1 * xv - alpha * G;
-          if (k == N - 1 && P.fix_f[i]) xn = zf[i];
+          for (int r = 0; r < NX; ++r) Gc = fma(a[r * NX], f[r], Gc);
+          const R G = last ? G0 : Gc;
+          // e_cost = -e_m on x_N (maximize m_N) folded into the same FMA
+          const R cost = (last && i == IM) ? alpha * wcost : R(0);
+          R xn = fma(-alpha, G, fma(c1, xv, cost));
+          xn = (last && P.fix_f[i]) ? zf[i] : xn;
           dx[o] = fma(R(2), xn, -xv);
           xt[o] = xv + rho * (xn - xv);
           if constexpr (chk) {
@@ -549,18 +557,23 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           phi[t] = pn;
         }
       } else {
+        // CTCS rows, one warp (N - 1 <= 31 lanes used; all lanes shuffle)
         const int k = t - PM;
+        R vn = 0;
         if (k < N - 1) {
           const R hy = dx[(k + 1) * NX + IY] - dx[k * NX + IY] - ep[k];
           const R v = vth[k];
           const R tn = max0(v + beta * hy);
-          vth[k] = v + rho * (tn - v);
+          vn = v + rho * (tn - v);
+          vth[k] = vn;
           if constexpr (chk) {
             const R old = th[k];
             rn = umax(rn, OB::nonneg(tn)); ro = umax(ro, OB::abs(old)); rd = umax(rd, OB::abs(tn - old));
           }
           th[k] = tn;
         }
+        const R vnext = __shfl_down_sync(0xffffffffu, vn, 1);
+        if (k < N - 1) td[k + 1] = vn - (k + 1 < N - 1 ? vnext : R(0));
       }
     }
     if constexpr (chk) {
@@ -628,16 +641,16 @@ template <> struct Vec16B<double> {
 };
 
 // Shared-memory offsets of the exchange vectors (inside the phase-local union
-// region, 16-byte aligned): vp[(N-1)][16], vt[32 + N], dx[N][16], du[N][NUP].
-struct RegLay { int vp, vt, dx, du, end; };
+// region, 16-byte aligned): vp[(N-1)][16], dx[N][16], du[N][NUP], td[N].
+struct RegLay { int vp, dx, du, td, end; };
 __host__ __device__ inline RegLay make_reg_lay(const Lay& L) {
   const int nup = L.nu <= 4 ? 4 : 8;
   RegLay Q;
   int o = (L.xt + 3) & ~3;
   Q.vp = o; o += (L.N - 1) * 16;
-  Q.vt = o; o += (L.N + 3) & ~3;
   Q.dx = o; o += L.N * 16;
   Q.du = o; o += L.N * nup;
+  Q.td = o; o += (L.N + 3) & ~3;  // CTCS-dual difference per node (as in phase_pipg)
   Q.end = o;
   return Q;
 }
@@ -682,9 +695,9 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
   const int RT = round32(nm), UT = round32(N * G);
   const RegLay Q = make_reg_lay(L);
   R* const vp = sm + Q.vp;
-  R* const vt = sm + Q.vt;
   R* const dxs = sm + Q.dx;
   R* const dus = sm + Q.du;
+  R* const tds = sm + Q.td;
   const bool row = tid < RT;
   const bool ctl = !row && tid < RT + UT;
   // row thread p = tid: dual row (interval kd, row i) and x task (node kx = kd + 1, component i)
@@ -698,6 +711,7 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
   const int ku = v / G, cc = v - G * (v / G);
   const bool has_u = ctl && ku < N && cc < NU;
   const bool has_th = ctl && v < N - 1;
+  const bool th_warp = ctl && v < 32;  // the control warp that holds the CTCS rows
   const bool has_x1 = ctl && v < NX;
   // registers.  Arrays: column of hat A^-_{kx} / row of hat A^-_{kd} / row of
   // hat B^-, hat B^+ (row thread); column of hat B^-_{ku} / of hat B^+_{ku-1}
@@ -755,9 +769,12 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
   if (has_th) {
     r6 = r5 = sm[L.th + v];
     r7 = sm[L.eps + v];
-    vt[v] = r5;
   }
   if (has_x1) { r8 = r9 = sm[L.xh + v]; r10 = sm[L.zi + v]; }
+  if (ctl && v >= 1 && v < N) tds[v] = sm[L.th + v - 1] - (v < N - 1 ? sm[L.th + v] : R(0));
+  const R s_iy = (has_d && i == IY) ? R(1) : R(0);
+  const R cost = (last_x && i == IM) ? alpha * R(P.w_cost) : R(0);
+  const int km = has_colA ? kx : 0;  // the last node has no A block (its column is zero)
   __syncthreads();
   const int jmax = force > 0 ? force : P.pipg_jmax;
   const int jcheck = P.pipg_jcheck;
@@ -766,15 +783,10 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
     U zn = 0, zo = 0, zd = 0, rn = 0, ro = 0, rd = 0;
     // ---- projected gradient step (primal)
     if (has_d) {
-      R G = -vp[kd * 16 + i];
-      if (has_colA) {
-        G = dot15_sm(a1, vp + kx * 16, G);
-        if (i == IY) G -= vt[kx];
-      }
-      if (i == IY) G += vt[kd];
-      if (last_x && i == IM) G -= R(P.w_cost);
-      R xn = c1 * r0 - alpha * G;
-      if (last_x && P.fix_f[i]) xn = sm[L.zf + i];
+      // branch-free (see phase_pipg): zero column for the last node
+      const R G = dot15_sm(a1, vp + km * 16, fma(s_iy, tds[kx], -vp[kd * 16 + i]));
+      R xn = fma(-alpha, G, fma(c1, r0, cost));
+      xn = (last_x && P.fix_f[i]) ? sm[L.zf + i] : xn;
       dxs[kx * 16 + i] = fma(R(2), xn, -r0);
       r0 += rho * (xn - r0);
       if constexpr (chk) { zn = umax(zn, OB::abs(xn)); zo = umax(zo, OB::abs(r1)); zd = umax(zd, OB::abs(xn - r1)); }
@@ -856,13 +868,16 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
       if constexpr (chk) { rn = umax(rn, OB::abs(pn)); ro = umax(ro, OB::abs(r7)); rd = umax(rd, OB::abs(pn - r7)); }
       r7 = pn;
       vp[kd * 16 + i] = r6;
-    } else if (has_th) {
-      const R hy = dxs[(v + 1) * 16 + IY] - dxs[v * 16 + IY] - r7;
-      const R tn = max0(r5 + beta * hy);
-      r5 += rho * (tn - r5);
-      if constexpr (chk) { rn = umax(rn, OB::nonneg(tn)); ro = umax(ro, OB::abs(r6)); rd = umax(rd, OB::abs(tn - r6)); }
-      r6 = tn;
-      vt[v] = r5;
+    } else if (th_warp) {
+      if (has_th) {
+        const R hy = dxs[(v + 1) * 16 + IY] - dxs[v * 16 + IY] - r7;
+        const R tn = max0(r5 + beta * hy);
+        r5 += rho * (tn - r5);
+        if constexpr (chk) { rn = umax(rn, OB::nonneg(tn)); ro = umax(ro, OB::abs(r6)); rd = umax(rd, OB::abs(tn - r6)); }
+        r6 = tn;
+      }
+      const R vnext = __shfl_down_sync(0xffffffffu, r5, 1);
+      if (has_th) tds[v + 1] = r5 - (v + 1 < N - 1 ? vnext : R(0));
     }
     if constexpr (chk) {
       U w6[6] = {zn, zo, zd, rn, ro, rd};
