@@ -454,25 +454,30 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           const int k = q / G, cc = q - G * k;
           const bool valid = k < N && cc < NU;
           const int o = k * NU + cc;
-          R uv = 0, un = 0;
-          if (valid) {
-            uv = ut[o];
-            R Gs = 0;
-            if (k < N - 1) {
-              const R* a = Bm + k * NX * NU + cc;
-              const R* f = vph + k * NX;
+          // branch-free like the x step: every lane runs both block products
+          // on valid blocks (node 0 has no B^+, node N no B^-, padding lanes
+          // neither) and selects discard what does not exist
+          const int kv = valid ? k : 0, cv = valid ? cc : 0;
+          const int km = kv < N - 1 ? kv : 0, kp = kv > 0 ? kv - 1 : 0;
+          const R uv = ut[kv * NU + cv];
+          R Gm = 0;
+          {
+            const R* a = Bm + km * NX * NU + cv;
+            const R* f = vph + km * NX;
 #pragma unroll
-              for (int r = 0; r < NX; ++r) Gs += a[r * NU] * f[r];
-            }
-            if (k > 0) {
-              const R* a = Bp + (k - 1) * NX * NU + cc;
-              const R* f = vph + (k - 1) * NX;
-#pragma unroll
-              for (int r = 0; r < NX; ++r) Gs += a[r * NU] * f[r];
-            }
-            un = c1 * uv - alpha * Gs;
-            if (cc == NU - 1) un = rmin(rmax(un, lo[k]), hi[k]);
+            for (int r = 0; r < NX; ++r) Gm = fma(a[r * NU], f[r], Gm);
           }
+          Gm = kv < N - 1 ? Gm : R(0);
+          R Gs = Gm;
+          {
+            const R* a = Bp + kp * NX * NU + cv;
+            const R* f = vph + kp * NX;
+#pragma unroll
+            for (int r = 0; r < NX; ++r) Gs = fma(a[r * NU], f[r], Gs);
+          }
+          Gs = kv > 0 ? Gs : Gm;
+          R un = c1 * uv - alpha * Gs;
+          if (cc == NU - 1) un = rmin(rmax(un, lo[kv]), hi[kv]);
           if (P.soc) {
             // project the node's thrust onto the sector (all lanes of the warp
             // take part in the shuffles; each group of G lanes is one node)
@@ -496,14 +501,14 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
             if (nT > tmax) { const R f = tmax / nT; T0 *= f; T1 *= f; T2 *= f; }
             if (valid && cc < 3) un = ((cc == 0 ? T0 : (cc == 1 ? T1 : T2)) - Tb) * ipT;
           }
-          if (valid) {
-            du[o] = fma(R(2), un, -uv);
-            ut[o] = uv + rho * (un - uv);
+          {
+            const R dn = fma(R(2), un, -uv), tn = uv + rho * (un - uv);
+            if (valid) { du[o] = dn; ut[o] = tn; }
             if constexpr (chk) {
-              const R old = uh[o];
-              zn = umax(zn, OB::abs(un)); zo = umax(zo, OB::abs(old)); zd = umax(zd, OB::abs(un - old));
+              const R old = uh[kv * NU + cv];
+              if (valid) { zn = umax(zn, OB::abs(un)); zo = umax(zo, OB::abs(old)); zd = umax(zd, OB::abs(un - old)); }
             }
-            uh[o] = un;
+            if (valid) uh[o] = un;
           }
         } else if (q < PG + NX) {
           // node 1: every component fixed by E_i
