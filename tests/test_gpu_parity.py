@@ -381,16 +381,23 @@ def test_fp32_error_report_n30(torch_cuda, oracle, inputs):
 
 
 def test_paper_model_paper256_distribution(torch_cuda, oracle, inputs):
-    """The paper's model (nu = 7, RCS torque) on the Monte Carlo distribution
-    of Sec. 7 with its limits (SCP <= 25, PIPG 2500): the runs converge and
+    """The paper's model (nu = 7, RCS torque) on the Monte Carlo of Sec. 7
+    (tests/golden/paper_sec7_monte_carlo.json: 256 runs, SCP <= 25, PIPG
+    2500, all converge in the paper): the runs converge and sampled ones
     match the oracle replay."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_sec7_monte_carlo.json")) as fh:
+        mc = json.load(fh)
     torch = torch_cuda
-    p = inputs.load_params(nu=7, scp_jmax=25, pipg_jmax=2500)
+    p = inputs.load_params(nu=7, scp_jmax=mc["scp_iteration_limit"], pipg_jmax=mc["pipg_iterations_per_subproblem"])
     from paper_2404_18034_gb300.pdg_mc import Solver
     S = Solver(p, 15)
-    x0 = inputs.dispersion(p, 32, inputs.config_seed(99), "paper256")
-    o = _solve_and_replay(torch, oracle, inputs, p, S, x0, None, 2, range(0, 32, 8))
+    n = mc["runs"]
+    x0 = inputs.dispersion(p, n, inputs.config_seed(99), "paper256")
+    o = _solve_and_replay(torch, oracle, inputs, p, S, x0, None, 2, range(0, n, 32), converged_only=True)
     assert np.mean(o["status"] == 0) >= 0.95
+    assert o["scp_iters"].max() <= mc["scp_iteration_limit"]
 
 
 def test_budget_status(torch_cuda, inputs):

@@ -79,11 +79,23 @@ def test_batch_matches_single(oracle, inputs, params):
         assert b["pipg_iters"][i] == r["pipg_iters"]
 
 
+def _paper_mc():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_sec7_monte_carlo.json")) as fh:
+        return json.load(fh)
+
+
 def test_paper_monte_carlo_distribution_converges(oracle, inputs):
-    """Sec. 7: r(0) ~ (U(6,9), U(3,6), U(1,2)), SCP <= 25, 2500 PIPG iterations:
-    every run converges (on this project's parameter set)."""
-    p = inputs.load_params(scp_jmax=25, pipg_jmax=2500)
-    x0 = inputs.dispersion(p, 24, inputs.config_seed(99), "paper256")
-    b = oracle.solve_batch(p, x0, np.full(24, 15, np.int32))
-    assert np.all(b["status"] == 0), b["status"]
-    assert b["scp_iters"].max() <= 25
+    """Sec. 7 (tests/golden/paper_sec7_monte_carlo.json): r(0) ~ (U(6,9),
+    U(3,6), U(1,2)), SCP <= 25, 2500 PIPG iterations: 256 of 256 runs
+    converge (on this project's parameter set)."""
+    mc = _paper_mc()
+    p = inputs.load_params(scp_jmax=mc["scp_iteration_limit"], pipg_jmax=mc["pipg_iterations_per_subproblem"])
+    n = mc["runs"]
+    x0 = inputs.dispersion(p, n, inputs.config_seed(99), "paper256")
+    for c, (lo, hi) in enumerate(mc["initial_position_bounds"]):
+        assert np.all((x0[:, 1 + c] >= lo) & (x0[:, 1 + c] <= hi))
+    b = oracle.solve_batch(p, x0, np.full(n, 15, np.int32))
+    assert int(np.sum(b["status"] == 0)) == mc["runs_converged"], np.bincount(b["status"])
+    assert b["scp_iters"].max() <= mc["scp_iteration_limit"]
