@@ -282,19 +282,21 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
     for (int t = tid; t < PX + PU + PM; t += T) {
       if (t < PX) {
         if (t < nx) {
+          // branch-free, as the PIPG x step: blocks that do not exist (the
+          // last node's A, the first node's coupling) run on valid data and
+          // selects discard them; the CTCS terms ride on a 0/1-weighted FMA
           const int k = t / NX, i = t - NX * k;
-          R g = 0;
-          if (k < N - 1) {
-            const R* a = Am + k * NX * NX + i;
-            const R* f = ph + k * NX;
+          const bool hasA = k < N - 1, hasP = k > 0;
+          const int ka = hasA ? k : 0, kp = hasP ? k - 1 : 0;
+          R gc = 0;
+          const R* a = Am + ka * NX * NX + i;
+          const R* f = ph + ka * NX;
 #pragma unroll
-            for (int r = 0; r < NX; ++r) g += a[r * NX] * f[r];
-            if (i == IY) g -= pt[k];
-          }
-          if (k > 0) {
-            g -= ph[(k - 1) * NX + i];
-            if (i == IY) g += pt[k - 1];
-          }
+          for (int r = 0; r < NX; ++r) gc = fma(a[r * NX], f[r], gc);
+          R g = hasA ? gc : R(0);
+          const R dth = (hasP ? pt[kp] : R(0)) - (hasA ? pt[ka] : R(0));
+          g = fma(i == IY ? R(1) : R(0), dth, g);
+          g -= hasP ? ph[kp * NX + i] : R(0);
           px[t] = g;
           s2 += g * g;
         }
@@ -302,19 +304,24 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
         const int q = t - PX;
         if (q < nuu) {
           const int k = q / NU, cc = q - NU * k;
-          R g = 0;
-          if (k < N - 1) {
-            const R* a = Bm + k * NX * NU + cc;
-            const R* f = ph + k * NX;
+          const bool hasM = k < N - 1, hasP = k > 0;
+          const int km = hasM ? k : 0, kp = hasP ? k - 1 : 0;
+          R gm = 0;
+          {
+            const R* a = Bm + km * NX * NU + cc;
+            const R* f = ph + km * NX;
 #pragma unroll
-            for (int r = 0; r < NX; ++r) g += a[r * NU] * f[r];
+            for (int r = 0; r < NX; ++r) gm = fma(a[r * NU], f[r], gm);
           }
-          if (k > 0) {
-            const R* a = Bp + (k - 1) * NX * NU + cc;
-            const R* f = ph + (k - 1) * NX;
+          gm = hasM ? gm : R(0);
+          R g = gm;
+          {
+            const R* a = Bp + kp * NX * NU + cc;
+            const R* f = ph + kp * NX;
 #pragma unroll
-            for (int r = 0; r < NX; ++r) g += a[r * NU] * f[r];
+            for (int r = 0; r < NX; ++r) g = fma(a[r * NU], f[r], g);
           }
+          g = hasP ? g : gm;
           pu[q] = g;
           s2 += g * g;
         }
