@@ -186,6 +186,21 @@ int pdg_mc_launch_info(pdg_handle* h, int* threads, int* ctas_per_sm, int* smem_
  * does not fit returns PDG_EINVAL. */
 int pdg_mc_set_threads(pdg_handle* h, int threads);
 
+/* Autotune the launch shape for this handle's n_max, nu and precision on a
+ * caller batch (no counterpart in the paper).  Times one solve of the batch
+ * (device x0 [B][14], n_nodes as in pdg_mc_solve_batch, execution mode 0/1/2)
+ * for every candidate: PIPG form 1 at 128..512 threads and form 2 from the
+ * threads it needs up to its limit, multiples of 32; candidates that do not
+ * fit on an SM are skipped.  Each candidate runs one untimed solve, then one
+ * solve timed with CUDA events on cuda_stream, scored by converged solves per
+ * second.  The fastest (form, threads) is applied to the handle (as by
+ * pdg_mc_set_pipg_form and pdg_mc_set_threads) and written to *threads_out,
+ * *form_out, *solves_per_s (each may be NULL).  Allocates and frees its
+ * scratch outputs; synchronizes the stream.  Returns PDG_EINVAL for B < 1 or
+ * no x0, or when no candidate ran (the handle's settings are then kept). */
+int pdg_mc_autotune(pdg_handle* h, int B, const double* x0, const int* n_nodes, int mode, int* threads_out,
+                    int* form_out, double* solves_per_s, void* cuda_stream);
+
 /* Choose how the PIPG loop (Alg. PIPG_custom, Sec. 4.3) is laid out on the
  * CTA.  Results agree to rounding; only speed differs.
  *   form 1: blocks hat A^-, hat B^+- and the iterates in shared memory, any

@@ -1,13 +1,14 @@
 """Autotuner for the launch shape of the batched solver.
 
-For one (device, n_max, nu, precision, execution form) it times a solve of a
-seeded batch at every candidate (PIPG layout, CTA size) pair -- the
-shared-memory PIPG form at multiples of 32 that leave room for at least one
-discretization interval and fit in shared memory, the register form from the
-threads it needs up to its limit -- keeps the fastest by converged solves per
-second, and records it in a JSON cache keyed by
+For one (device, n_max, nu, precision, execution form) the library's
+pdg_mc_autotune times a solve of a seeded batch at every candidate (PIPG
+layout, CTA size) pair -- the shared-memory PIPG form at 128..512 threads, the
+register form from the threads it needs up to its limit, candidates that do
+not fit skipped -- and keeps the fastest by converged solves per second; this
+module records the choice in a JSON cache keyed by
 "device|n_max|nu|precision|mode".  Solver(tune_cache=...) applies a cached
-choice through pdg_mc_set_pipg_form and pdg_mc_set_threads.
+choice through pdg_mc_set_pipg_form and pdg_mc_set_threads.  candidates()
+lists the pairs that fit, for tests and reports.
 
   python -m paper_2404_18034_gb300.autotune --nodes 15 --precision fp64 --batch 2048
 """
@@ -86,8 +87,9 @@ def _fitting(ts: Iterable[int], n_max: int, nu: int, precision: int) -> Iterable
 
 
 def autotune(params: Dict, n_max: int, precision: int = 0, mode: int = 1, batch: int = 2048, seed: int = 7,
-             reps: int = 2, path: str = DEFAULT_CACHE, cands: Optional[Iterable[Tuple[int, int]]] = None,
-             forms: Iterable[int] = (1, 2)) -> Dict:
+             path: str = DEFAULT_CACHE) -> Dict:
+    """Run the library's autotuner (pdg_mc_autotune: every (PIPG form, CTA
+    size) candidate timed on a seeded batch) and record its choice."""
     import torch
 
     from . import inputs
@@ -96,29 +98,9 @@ def autotune(params: Dict, n_max: int, precision: int = 0, mode: int = 1, batch:
     name = torch.cuda.get_device_name(dev)
     x0 = torch.from_numpy(inputs.dispersion(params, batch, seed, "bj")).to(dev)
     S = Solver(params, n_max, precision)
-    results = {}
-    for form, t in (cands or candidates(n_max, int(params["nu"]), precision, forms)):
-        S.set_pipg_form(form)
-        S.set_threads(t)
-        try:
-            S.solve(x0, mode=mode)
-            torch.cuda.synchronize()
-        except RuntimeError:
-            continue
-        best = None
-        for _ in range(reps):
-            t0 = time.perf_counter()
-            out = S.solve(x0, mode=mode)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            conv = int((out["status"] == 0).sum().item())
-            rate = conv / dt
-            best = rate if best is None else max(best, rate)
-        results[(form, t)] = best
+    threads, form, rate = S.autotune(x0, None, mode)
     S.close()
-    f_best, t_best = max(results, key=results.get)
-    entry = {"threads": int(t_best), "form": int(f_best), "solves_per_s": results[(f_best, t_best)], "batch": batch,
-             "swept": {f"form{f}:{k}": v for (f, k), v in sorted(results.items())}}
+    entry = {"threads": int(threads), "form": int(form), "solves_per_s": float(rate), "batch": batch}
     cache = load_cache(path)
     cache[cache_key(name, n_max, int(params["nu"]), precision, mode)] = entry
     with open(path, "w") as fh:
@@ -135,14 +117,12 @@ def main():
     ap.add_argument("--batch", type=int, default=2048)
     ap.add_argument("--nu", type=int, default=4)
     ap.add_argument("--cache", default=DEFAULT_CACHE)
-    ap.add_argument("--forms", type=int, nargs="+", default=[1, 2], choices=[1, 2])
     a = ap.parse_args()
     p = inputs.load_params(nu=a.nu)
     for n in a.nodes:
         for pr in a.precision:
             for m in a.mode:
-                e = autotune(p, n, 0 if pr == "fp64" else 1, 1 if m == "persistent" else 0, a.batch, path=a.cache,
-                             forms=a.forms)
+                e = autotune(p, n, 0 if pr == "fp64" else 1, 1 if m == "persistent" else 0, a.batch, path=a.cache)
                 print(json.dumps({"nodes": n, "precision": pr, "mode": m, **e}))
 
 

@@ -1329,6 +1329,83 @@ int pdg_mc_set_pipg_form(pdg_handle* h, int form) {
 
 int pdg_mc_pipg_form(const pdg_handle* h) { return h ? h->last_variant : PDG_EINVAL; }
 
+int pdg_mc_autotune(pdg_handle* h, int B, const double* x0, const int* n_nodes, int mode, int* threads_out,
+                    int* form_out, double* solves_per_s, void* cuda_stream) {
+  if (!h) return PDG_EINVAL;
+  h->err.clear();
+  if (B < 1 || !x0) return fail(h, PDG_EINVAL, "autotune needs B >= 1 and x0");
+  if (mode < 0 || mode > 2) return fail(h, PDG_EINVAL, "mode must be 0, 1 or 2");
+  PDG_CUDA(h, cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int nu = h->p.nu, n = h->n_max;
+  // caller-invisible outputs of the trial solves
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t bX = sizeof(double) * (size_t)B * n * NX, bU = sizeof(double) * (size_t)B * n * nu;
+  const size_t need = al(bX) + al(bU) + 2 * al(sizeof(double) * B) + 2 * al(sizeof(int) * B) + al(sizeof(long long) * B);
+  char* buf = nullptr;
+  PDG_CUDA(h, cudaMalloc(&buf, need));
+  char* c = buf;
+  double* X = (double*)c; c += al(bX);
+  double* U = (double*)c; c += al(bU);
+  double* tf = (double*)c; c += al(sizeof(double) * B);
+  double* fu = (double*)c; c += al(sizeof(double) * B);
+  int* st = (int*)c; c += al(sizeof(int) * B);
+  int* sc = (int*)c; c += al(sizeof(int) * B);
+  long long* pi = (long long*)c;
+  int* hst = (int*)malloc(sizeof(int) * B);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int keep_t = h->threads_override, keep_f = h->pipg_variant;
+  double best = -1.0;
+  int best_t = 0, best_f = 0, rc = PDG_OK;
+  const int treg = pipg_reg_threads(n, nu), maxt = h->p.precision == 1 ? PDG_REG_MAXT_F32 : 512;
+  // candidates: (form 1, 128..512) and (form 2, its minimum .. its limit), multiples of 32
+  for (int form = 1; form <= 2 && rc == PDG_OK; ++form) {
+    const int t_lo = form == 1 ? 128 : treg, t_hi = form == 1 ? 512 : maxt;
+    for (int T = t_lo; T <= t_hi && rc == PDG_OK; T += 32) {
+      h->pipg_variant = form;
+      h->threads_override = T;
+      // a candidate that does not fit (shared memory, threads) is skipped
+      if (pdg_mc_solve_batch(h, B, x0, n_nodes, mode, X, U, tf, fu, st, sc, pi, nullptr, s) != PDG_OK) {
+        h->err.clear();
+        if (cudaGetLastError() != cudaSuccess) { rc = fail(h, PDG_ECUDA, "autotune: CUDA error after a skipped candidate"); }
+        continue;
+      }
+      if (cudaEventRecord(e0, s) != cudaSuccess) { rc = fail(h, PDG_ECUDA, "autotune: event"); break; }
+      int r2 = pdg_mc_solve_batch(h, B, x0, n_nodes, mode, X, U, tf, fu, st, sc, pi, nullptr, s);
+      if (r2 != PDG_OK) { rc = r2; break; }
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaMemcpy(hst, st, sizeof(int) * B, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = fail(h, PDG_ECUDA, "autotune: timing or status copy failed");
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      int conv = 0;
+      for (int b = 0; b < B; ++b) conv += hst[b] == PDG_CONVERGED;
+      const double rate = ms > 0 ? conv / (ms * 1e-3) : 0.0;
+      if (rate > best) { best = rate; best_t = T; best_f = form; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  free(hst);
+  cudaFree(buf);
+  if (rc != PDG_OK || best_t == 0) {
+    h->threads_override = keep_t;
+    h->pipg_variant = keep_f;
+    return rc != PDG_OK ? rc : fail(h, PDG_EINVAL, "autotune: no candidate ran");
+  }
+  h->threads_override = best_t;
+  h->pipg_variant = best_f;
+  if (threads_out) *threads_out = best_t;
+  if (form_out) *form_out = best_f;
+  if (solves_per_s) *solves_per_s = best;
+  return PDG_OK;
+}
+
 int pdg_mc_set_threads(pdg_handle* h, int threads) {
   if (!h) return PDG_EINVAL;
   if (threads < 0 || threads > PDG_REG_MAXT_F32 || (threads % 32) != 0)

@@ -23,7 +23,8 @@ ERRORS = {-1: "PDG_EINVAL", -2: "PDG_ENOMEM", -3: "PDG_ECUDA"}
 EXPORTS = ("pdg_mc_init", "pdg_mc_destroy", "pdg_mc_last_error", "pdg_mc_solve_batch",
            "pdg_mc_solve_batch_host", "pdg_mc_subproblem", "pdg_mc_scp_step", "pdg_mc_launch_info",
            "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc",
-           "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form", "pdg_mc_probe_fma_lanes")
+           "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form", "pdg_mc_probe_fma_lanes",
+           "pdg_mc_autotune")
 
 
 class PdgParams(C.Structure):
@@ -79,11 +80,13 @@ def load_library(path: str = LIB_PATH):
     L.pdg_mc_grad_batch.argtypes = [_VP, C.c_int] + [_VP] * 8 + [_VP]
     L.pdg_mc_set_pipg_form.argtypes = [_VP, C.c_int]
     L.pdg_mc_probe_fma_lanes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), _VP]
+    L.pdg_mc_autotune.argtypes = [_VP, C.c_int, _VP, _VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_double), _VP]
     L.pdg_mc_pipg_form.argtypes = [_VP]
     for name in ("pdg_mc_init", "pdg_mc_solve_batch", "pdg_mc_solve_batch_host", "pdg_mc_subproblem",
                  "pdg_mc_scp_step", "pdg_mc_launch_info", "pdg_mc_set_threads", "pdg_mc_probe_fma",
                  "pdg_mc_solve_batch_noalloc", "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form",
-                 "pdg_mc_probe_fma_lanes"):
+                 "pdg_mc_probe_fma_lanes", "pdg_mc_autotune"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -300,6 +303,16 @@ class Solver:
         self._check(self.lib.pdg_mc_launch_info(self.h, C.byref(t), C.byref(c), C.byref(s)), "pdg_mc_launch_info")
         return dict(threads=t.value, ctas_per_sm=c.value, smem_bytes=s.value,
                     pipg_form=int(self.lib.pdg_mc_pipg_form(self.h)))
+
+    def autotune(self, x0, n_nodes=None, mode: int = 1, stream=None):
+        """pdg_mc_autotune on a device batch: returns (threads, form,
+        converged solves/s) of the fastest candidate, applied to the handle."""
+        t, f, r = C.c_int(), C.c_int(), C.c_double()
+        rc = self.lib.pdg_mc_autotune(self.h, int(x0.shape[0]), _ptr(x0), _ptr(n_nodes), int(mode), C.byref(t),
+                                      C.byref(f), C.byref(r), self._stream(stream))
+        self._check(rc, "pdg_mc_autotune")
+        self.tuned_threads, self.tuned_form = t.value, f.value
+        return t.value, f.value, r.value
 
     def set_pipg_form(self, form: int):
         """0 automatic, 1 blocks in shared memory, 2 blocks in registers."""
