@@ -350,10 +350,11 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
 // extrapolated dual of the dynamics rows; the stop test compares iterates j+1
 // and j (the warm start being iterate 0).
 // Work split, every task range padded to whole warps:
-//   primal phase: x_hat of nodes 2..N (15 (N-1) tasks), then u_hat (N nu
-//     tasks) and the fixed node 1 (15 tasks);
+//   primal phase: x_hat of nodes 2..N (15 (N-1) tasks), then u_hat (G lanes
+//     per node) and the fixed node 1 (15 tasks);
 //   dual phase: row i of interval k updates mu^+-, nu^+- (they read the same
-//     extrapolated dual entry) and then phi; then the CTCS rows theta_k.
+//     extrapolated dual entry) and then phi; then the CTCS rows theta_k, whose
+//     warp also forms the per-node differences td for the next primal step.
 template <bool B> struct ChkTag { static constexpr bool value = B; };
 
 // Returns the iterations run.  Extrapolations 2 z - z~ are written as fma:
@@ -619,16 +620,19 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
 // Alg. stopping), mapped so that nothing but the two exchanged vectors goes
 // through shared memory in the loop.  Thread roles are warp-uniform:
 //  * row threads p < RT = round32((N-1) NX): x task p (node p/NX + 1,
-//    component i = p%NX; it keeps column i of hat A^-_{node}) and dual row p
-//    (interval p/NX, row i; it keeps row i of hat A^-, hat B^-, hat B^+, hat w
-//    and its mu+-, phi entries).  Threads p < NX also own node 1.
+//    component i = p%NX; it keeps column i of hat A^-_{node}, zero for the
+//    last node) and dual row p (interval p/NX, row i; it keeps row i of
+//    hat A^-, hat B^-, hat B^+, hat w and its mu+-, phi entries).
 //  * control threads v = tid - RT < UT = round32(N G): node v/G, control
 //    component v%G (G lanes per node so a node's thrust is one aligned lane
 //    group for the cone projection); they keep column v%G of hat B^-_{node}
-//    and hat B^+_{node-1}.  In the dual step threads v < N-1 own theta_v.
-// Exchanged through shared memory: the relaxed dual (phi~, theta~) read by the
-// primal step and the extrapolated primal (2 z_{j+1} - z~_j) read by the dual
-// step, node vectors padded to 16 entries so they load as 16-byte vectors.
+//    and hat B^+_{node-1}.  Threads v < NX also own node 1, and in the dual
+//    step threads v < N-1 own theta_v.
+// Exchanged through shared memory: the relaxed dual phi~ and the per-node
+// difference of the relaxed CTCS duals (td, as in phase_pipg) read by the
+// primal step, and the extrapolated primal (2 z_{j+1} - z~_j) read by the
+// dual step; node vectors are padded to 16 entries so they load as 16-byte
+// vectors.
 // Needs blockDim.x >= pipg_reg_threads(N, NU).
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int pipg_reg_groups(int nu) { return nu <= 4 ? 4 : 8; }
