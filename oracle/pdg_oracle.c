@@ -40,14 +40,30 @@
 #include <omp.h>
 #endif
 
+/* The problem template of Sec. 2 (F, g, boundary conditions, Mayer cost) is
+ * instantiated by a model chosen when this file is compiled:
+ *   default          the 6-DoF model of Sec. 5, x = (m, r, v, q, omega, y);
+ *   ORC_MODEL_3DOF   the translational (3-DoF) model Sec. 1 contrasts it with,
+ *                    x = (m, r, v, y): point mass, thrust in the inertial
+ *                    frame, no attitude (readings R18-R19).
+ * Everything past the model section uses only NX, XM (the cost's mass) and XY
+ * (the CTCS integrator, always last). */
+#ifdef ORC_MODEL_3DOF
+#define NX 8
+enum { XM = 0, XR = 1, XV = 4, XY = 7 };
+#else
 #define NX 15
 enum { XM = 0, XR = 1, XV = 4, XQ = 7, XW = 11, XY = 14 };
+#endif
+
+int orc_nx(void) { return NX; }
 
 /* ------------------------------------------------------------------------ */
 /* Sec. 5: model                                                             */
 /* ------------------------------------------------------------------------ */
 
 /* C_{I<-B}(q), Hamilton scalar-first (R1). */
+#ifndef ORC_MODEL_3DOF
 static void dcm(const double* q, double C[3][3]) {
   double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
   C[0][0] = 1.0 - 2.0 * (q2 * q2 + q3 * q3);
@@ -175,21 +191,6 @@ int orc_g(const orc_params* p, const double* x, const double* u, double* g) {
   return ng;
 }
 
-/* f(x, u) = s (F, 1^T |g|_+^2), Eq. sys-dyn-dil-aug (no h in this problem). */
-void orc_f(const orc_params* p, const double* x, const double* u, double* f) {
-  double s = u[p->nu - 1];
-  double Fx[14], g[10];
-  orc_F(p, x, u, Fx);
-  int ng = orc_g(p, x, u, g);
-  double pen = 0;
-  for (int i = 0; i < ng; i++) {
-    double gp = g[i] > 0 ? g[i] : 0;
-    pen += gp * gp;
-  }
-  for (int i = 0; i < 14; i++) f[i] = s * Fx[i];
-  f[14] = s * pen;
-}
-
 /* A = df/dx (15x15), B = df/du (15 x nu), dense, analytic. */
 void orc_jac(const orc_params* p, const double* x, const double* u, double* A, double* B) {
   const int nu = p->nu;
@@ -203,7 +204,7 @@ void orc_jac(const orc_params* p, const double* x, const double* u, double* A, d
   memset(B, 0, sizeof(double) * NX * nu);
 #define AA(i, j) A[(i) * NX + (j)]
 #define BB(i, j) B[(i) * nu + (j)]
-  double Fx[14], g[10];
+  double Fx[NX - 1], g[10];
   orc_F(p, x, u, Fx);
   int ng = orc_g(p, x, u, g);
   double gp[10];
@@ -285,6 +286,106 @@ void orc_jac(const orc_params* p, const double* x, const double* u, double* A, d
   BB(XY, nu - 1) = pen;
 #undef AA
 #undef BB
+}
+
+#else /* ORC_MODEL_3DOF */
+
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* 3-DoF F(xi, zeta): mass depletion with the thrust magnitude, r' = v,
+ * v' = T / m + g; T is an inertial-frame vector (R18). */
+void orc_F(const orc_params* p, const double* x, const double* u, double* Fx) {
+  const double* v = x + XV;
+  const double* T = u;
+  Fx[0] = -p->alpha_mdot * sqrt(dot3(T, T));
+  for (int i = 0; i < 3; i++) Fx[1 + i] = v[i];
+  for (int i = 0; i < 3; i++) Fx[4 + i] = T[i] / x[XM] + p->g_I[i];
+}
+
+/* 3-DoF g (R19): dry mass, altitude, speed, thrust pointing within delta_max
+ * of the up axis (the 6-DoF gimbal row with the body axis taken as up),
+ * thrust magnitude bounds, and the optional glide-slope row of the 6-DoF
+ * model.  Row order: m, r_x, v, pointing, T_max, T_min[, glide slope]. */
+int orc_g(const orc_params* p, const double* x, const double* u, double* g) {
+  const double* r = x + XR;
+  const double* v = x + XV;
+  const double* T = u;
+  double nT = sqrt(dot3(T, T));
+  g[0] = p->m_dry - x[XM];
+  g[1] = -r[0];
+  g[2] = dot3(v, v) - p->v_max * p->v_max;
+  g[3] = nT - T[0] / cos(p->delta_max);
+  g[4] = nT - p->T_max;
+  if (p->soc_thrust) { g[3] = -1.0; g[4] = -1.0; }  /* imposed by projection instead */
+  g[5] = p->T_min - nT;
+  int ng = 6;
+  if (p->glide_slope) g[ng++] = p->tan_gs * p->tan_gs * (r[1] * r[1] + r[2] * r[2]) - r[0] * r[0];
+  return ng;
+}
+
+/* A = df/dx (8x8), B = df/du (8 x 4), dense, analytic. */
+void orc_jac(const orc_params* p, const double* x, const double* u, double* A, double* B) {
+  const int nu = p->nu;
+  const double s = u[nu - 1];
+  const double m = x[XM];
+  const double* v = x + XV;
+  const double* T = u;
+  memset(A, 0, sizeof(double) * NX * NX);
+  memset(B, 0, sizeof(double) * NX * nu);
+#define AA(i, j) A[(i) * NX + (j)]
+#define BB(i, j) B[(i) * nu + (j)]
+  double Fx[NX - 1], g[10], gp[10];
+  orc_F(p, x, u, Fx);
+  int ng = orc_g(p, x, u, g);
+  double pen = 0;
+  for (int i = 0; i < ng; i++) {
+    gp[i] = g[i] > 0 ? g[i] : 0;
+    pen += gp[i] * gp[i];
+  }
+  double nT = sqrt(dot3(T, T));
+  double Tu[3] = {0, 0, 0}; /* dn/dT (R3) */
+  if (nT > 0) for (int i = 0; i < 3; i++) Tu[i] = T[i] / nT;
+  for (int i = 0; i < 3; i++) {
+    AA(XR + i, XV + i) = s;
+    AA(XV + i, XM) = s * (-T[i] / (m * m));
+  }
+  /* y row: sum_i 2 |g_i|_+ dg_i/dx */
+  AA(XY, XM) += s * 2.0 * gp[0] * (-1.0);
+  AA(XY, XR + 0) += s * 2.0 * gp[1] * (-1.0);
+  for (int i = 0; i < 3; i++) AA(XY, XV + i) += s * 2.0 * gp[2] * (2.0 * v[i]);
+  if (p->glide_slope) {
+    const double ggs = gp[ng - 1], t2 = p->tan_gs * p->tan_gs;
+    AA(XY, XR + 0) += s * 2.0 * ggs * (-2.0 * x[XR + 0]);
+    AA(XY, XR + 1) += s * 2.0 * ggs * (2.0 * t2 * x[XR + 1]);
+    AA(XY, XR + 2) += s * 2.0 * ggs * (2.0 * t2 * x[XR + 2]);
+  }
+  for (int j = 0; j < 3; j++) {
+    BB(XM, j) = s * (-p->alpha_mdot * Tu[j]);
+    BB(XV + j, j) = s / m;
+    double dg3 = Tu[j] - (j == 0 ? 1.0 / cos(p->delta_max) : 0.0);
+    BB(XY, j) = s * 2.0 * (gp[3] * dg3 + gp[4] * Tu[j] - gp[5] * Tu[j]);
+  }
+  for (int i = 0; i < NX - 1; i++) BB(i, nu - 1) = Fx[i];
+  BB(XY, nu - 1) = pen;
+#undef AA
+#undef BB
+}
+
+#endif /* ORC_MODEL_3DOF */
+
+/* f(x, u) = s (F, 1^T |g|_+^2), Eq. sys-dyn-dil-aug (no h in this problem). */
+void orc_f(const orc_params* p, const double* x, const double* u, double* f) {
+  double s = u[p->nu - 1];
+  double Fx[NX - 1], g[10];
+  orc_F(p, x, u, Fx);
+  int ng = orc_g(p, x, u, g);
+  double pen = 0;
+  for (int i = 0; i < ng; i++) {
+    double gp = g[i] > 0 ? g[i] : 0;
+    pen += gp * gp;
+  }
+  for (int i = 0; i < NX - 1; i++) f[i] = s * Fx[i];
+  f[XY] = s * pen;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -469,7 +570,7 @@ void orc_scale(const orc_params* p, int N, const double* x0, const double* X, co
   }
   /* hat z_i: E_i selects all of xi, with y_1 = 0 appended (Eq. disc-ocp) */
   for (int i = 0; i < NX; i++) {
-    double zi = (i < 14) ? x0[i] : 0.0;
+    double zi = (i < NX - 1) ? x0[i] : 0.0;
     qp->zi[i] = (zi - X[i]) / Px[i];
     qp->fixf[i] = p->fix_f[i];
     qp->zf[i] = p->fix_f[i] ? (p->z_f[i] - X[(N - 1) * NX + i]) / Px[i] : 0.0;
@@ -956,6 +1057,7 @@ double orc_sym_eig_max(int n, double* M) {
 /* Sec. 2.3: SCP                                                            */
 /* ------------------------------------------------------------------------ */
 
+#ifndef ORC_MODEL_3DOF
 /* Initial guess (Sec. 5 asks for "an appropriate" one; this reading):
  * straight lines in r, v, omega from x0 to z_f; normalized linear
  * interpolation of q from x0 to z_f; mass linear from m_wet to
@@ -989,6 +1091,30 @@ void orc_init_guess(const orc_params* p, int N, const double* x0, double* X, dou
     u[nu - 1] = p->tf_guess;
   }
 }
+#else
+/* Initial guess of the 3-DoF model, the 6-DoF one without attitude: straight
+ * lines in r, v from x0 to z_f, mass linear from m_wet to (m_wet + m_dry)/2,
+ * y = 0, hover thrust m ||g|| along the up axis, s = tf_guess. */
+void orc_init_guess(const orc_params* p, int N, const double* x0, double* X, double* U) {
+  const int nu = p->nu;
+  double g0 = sqrt(dot3(p->g_I, p->g_I));
+  double mf = 0.5 * (x0[XM] + p->m_dry);
+  for (int k = 0; k < N; k++) {
+    double t = (double)k / (N - 1);
+    double* x = X + k * NX;
+    x[XM] = (1.0 - t) * x0[XM] + t * mf;
+    for (int i = 0; i < 3; i++) {
+      x[XR + i] = (1.0 - t) * x0[XR + i] + t * p->z_f[XR + i];
+      x[XV + i] = (1.0 - t) * x0[XV + i] + t * p->z_f[XV + i];
+    }
+    x[XY] = 0.0;
+    double* u = U + k * nu;
+    for (int c = 0; c < nu; c++) u[c] = 0.0;
+    u[0] = x[XM] * g0;
+    u[nu - 1] = p->tf_guess;
+  }
+}
+#endif
 
 int orc_scp_iterate(const orc_params* p, int N, const double* x0, double* X, double* U,
                     orc_pd* ws, int force_pow, int force_pipg, double force_sigma,
@@ -1093,7 +1219,7 @@ int orc_solve_batch(const orc_params* p, int B, int Nmax, const int* Ns, const d
   for (int b = 0; b < B; b++) {
     int N = Ns ? Ns[b] : Nmax;
     orc_result r;
-    orc_solve(p, N, x0s + (size_t)b * 14, X + (size_t)b * Nmax * NX, U + (size_t)b * Nmax * nu, &r, NULL, 0, 0);
+    orc_solve(p, N, x0s + (size_t)b * (NX - 1), X + (size_t)b * Nmax * NX, U + (size_t)b * Nmax * nu, &r, NULL, 0, 0);
     if (tf) tf[b] = r.tf;
     if (fuel) fuel[b] = r.fuel;
     if (status) status[b] = r.status;

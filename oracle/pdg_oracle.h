@@ -12,10 +12,20 @@
  * "Alg." in the implementation.  Readings of silent or garbled passages are
  * listed next to the code that takes them.
  *
+ * The model (F, g and the initial guess of the problem template of Sec. 2)
+ * is chosen when the library is compiled: libpdg_oracle.so holds the 6-DoF
+ * model of Sec. 5, libpdg_oracle_3dof.so (-DORC_MODEL_3DOF) the translational
+ * 3-DoF model.  orc_nx() returns the library's state size NX.
+ *
  * Layouts (row-major, double):
- *   state  x[15]  = (m, r[3], v[3], q[4], omega[3], y)      (Sec. 2.1, Sec. 5)
- *   control u[nu] = (T[3], [gamma[3],] s), nu in {4, 7}     (Sec. 2.1, Sec. 5)
- *   X[N][15], U[N][nu]; A[N-1][15][15]; Bm, Bp[N-1][15][nu]; xprop[N-1][15]
+ *   6-DoF state x[15] = (m, r[3], v[3], q[4], omega[3], y)   (Sec. 2.1, Sec. 5)
+ *   3-DoF state x[8]  = (m, r[3], v[3], y)
+ *   control u[nu] = (T[3], [gamma[3],] s), nu in {4, 7}; the 3-DoF model has nu = 4
+ *   X[N][NX], U[N][nu]; A[N-1][NX][NX]; Bm, Bp[N-1][NX][nu]; xprop[N-1][NX]
+ *   x0 (the initial condition of a solve) is the first NX - 1 entries of x.
+ * Parameter arrays below are sized for the 6-DoF model; the 3-DoF model reads
+ * the first NX entries of z_f, fix_f and P_x, and uses delta_max as the
+ * half-angle of its thrust-pointing cone about the up axis.
  */
 #ifndef PDG_ORACLE_H
 #define PDG_ORACLE_H
@@ -57,11 +67,11 @@ typedef struct orc_params {
 /* Scaled convex subproblem data (Eq. cvx-subproblem-custom). */
 typedef struct orc_qp {
   int N, nu;
-  double *Am;   /* [N-1][15][15]  hat A^-_k */
-  double *Ap;   /* [N-1][15][15]  hat A^+_k = -I */
-  double *Bm;   /* [N-1][15][nu]  hat B^-_k */
-  double *Bp;   /* [N-1][15][nu]  hat B^+_k */
-  double *w;    /* [N-1][15]      hat w_k */
+  double *Am;   /* [N-1][NX][NX]  hat A^-_k */
+  double *Ap;   /* [N-1][NX][NX]  hat A^+_k = -I */
+  double *Bm;   /* [N-1][NX][nu]  hat B^-_k */
+  double *Bp;   /* [N-1][NX][nu]  hat B^+_k */
+  double *w;    /* [N-1][NX]      hat w_k */
   double *eps;  /* [N-1]          hat epsilon_k */
   double *umin; /* [N][nu]        hat u_{k,min} (-inf where unbounded) */
   double *umax; /* [N][nu]        hat u_{k,max} (+inf where unbounded) */
@@ -77,18 +87,19 @@ typedef struct orc_qp {
 
 /* PIPG primal-dual state (warm start in, solution out), Alg. PIPG_custom. */
 typedef struct orc_pd {
-  double *xh;   /* [N][15] */
+  double *xh;   /* [N][NX] */
   double *uh;   /* [N][nu] */
-  double *mup;  /* [N-1][15] */
-  double *mum;  /* [N-1][15] */
-  double *phi;  /* [N-1][15] */
+  double *mup;  /* [N-1][NX] */
+  double *mum;  /* [N-1][NX] */
+  double *phi;  /* [N-1][NX] */
   double *th;   /* [N-1] */
 } orc_pd;
 
 /* ---- model (Sec. 5) ---- */
-void orc_F(const orc_params* p, const double* x, const double* u, double* Fx);   /* dxi/dt, 14 */
+int  orc_nx(void);                                                                /* NX */
+void orc_F(const orc_params* p, const double* x, const double* u, double* Fx);   /* dxi/dt, NX - 1 */
 int  orc_g(const orc_params* p, const double* x, const double* u, double* g);    /* returns n_g */
-void orc_f(const orc_params* p, const double* x, const double* u, double* f);    /* Eq. sys-dyn-dil-aug, 15 */
+void orc_f(const orc_params* p, const double* x, const double* u, double* f);    /* Eq. sys-dyn-dil-aug, NX */
 void orc_jac(const orc_params* p, const double* x, const double* u, double* A, double* B);
 
 /* ---- discretization (Sec. 3.2, Sec. 3.3.1) ---- */
@@ -164,7 +175,7 @@ int orc_solve(const orc_params* p, int N, const double* x0, double* X, double* U
               orc_result* res, int* trace, int replay, int replay_scp);
 
 /* Batch over instances with OpenMP (nthreads <= 0: library default).
- * X: [B][Nmax][15], U: [B][Nmax][nu]; N may differ per instance. */
+ * x0s: [B][NX-1], X: [B][Nmax][NX], U: [B][Nmax][nu]; N may differ per instance. */
 int orc_solve_batch(const orc_params* p, int B, int Nmax, const int* Ns, const double* x0s,
                     double* X, double* U, double* tf, double* fuel, int* status,
                     int* scp_iters, long long* pipg_iters, int nthreads);

@@ -1,8 +1,11 @@
 """ctypes front end of the FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
 
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this module.  It builds ``libpdg_oracle.so`` from
-``pdg_oracle.c`` with gcc and exposes the oracle's routines on numpy arrays.
+``bench.py`` may import this module.  It builds ``libpdg_oracle.so`` (the
+6-DoF model of Sec. 5) and ``libpdg_oracle_3dof.so`` (the translational 3-DoF
+model) from ``pdg_oracle.c`` with gcc and exposes the oracle's routines on
+numpy arrays; every routine picks the library by the parameter dict's
+``model`` ("6dof" when absent), and state arrays have that model's size NX.
 It shares no code with the CUDA solver; the two meet only in the parameter
 dict and the initial conditions produced by ``paper_2404_18034_gb300.inputs``.
 """
@@ -19,24 +22,46 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pdg_oracle.c")
-_LIB = os.path.join(_HERE, "libpdg_oracle.so")
-NX = 15
+_LIBS = {"6dof": os.path.join(_HERE, "libpdg_oracle.so"), "3dof": os.path.join(_HERE, "libpdg_oracle_3dof.so")}
+_DEFS = {"6dof": [], "3dof": ["-DORC_MODEL_3DOF"]}
+NXS = {"6dof": 15, "3dof": 8}
+NX = NXS["6dof"]
 _lock = threading.Lock()
-_lib = None
+_libs: Dict = {}
+
+
+def model_of(p: Dict) -> str:
+    m = p.get("model", "6dof")
+    if m not in NXS:
+        raise ValueError(f"unknown model {m!r}")
+    return m
+
+
+def nx_of(p: Dict) -> int:
+    """State size NX of the parameter dict's model (15 or 8)."""
+    return NXS[model_of(p)]
+
+
+def _build_one(model: str, force: bool) -> str:
+    out = _LIBS[model]
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= max(os.path.getmtime(_SRC),
+                                             os.path.getmtime(os.path.join(_HERE, "pdg_oracle.h")))):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-Wall"] + _DEFS[model] + \
+        [_SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, out)
+    return out
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (plain C, -O2, OpenMP) next to its source."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
-                                              os.path.getmtime(os.path.join(_HERE, "pdg_oracle.h")))):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-Wall",
-           _SRC, "-o", tmp, "-lm"]
-    subprocess.check_call(cmd)
-    os.replace(tmp, _LIB)
-    return _LIB
+    """Compile both model libraries of the oracle (plain C, -O2, OpenMP)
+    next to their source; returns the 6-DoF one's path."""
+    for m in ("3dof", "6dof"):
+        path = _build_one(m, force)
+    return path
 
 
 class Params(C.Structure):
@@ -91,12 +116,13 @@ class Result(C.Structure):
                 ("defect", C.c_double), ("step", C.c_double)]
 
 
-def lib():
-    global _lib
+def lib(model: str = "6dof"):
     with _lock:
-        if _lib is None:
-            build()
-            L = C.CDLL(_LIB)
+        if model not in _libs:
+            L = C.CDLL(_build_one(model, False))
+            L.orc_nx.restype = C.c_int
+            if L.orc_nx() != NXS[model]:
+                raise RuntimeError(f"oracle library for {model} reports NX = {L.orc_nx()}")
             P = C.POINTER(Params)
             L.orc_F.argtypes = [P, _DP, _DP, _DP]
             L.orc_g.argtypes = [P, _DP, _DP, _DP]
@@ -127,8 +153,12 @@ def lib():
             L.orc_solve.argtypes = [P, C.c_int, _DP, _DP, _DP, C.POINTER(Result), _IP, C.c_int, C.c_int]
             L.orc_solve_batch.argtypes = [P, C.c_int, C.c_int, _IP, _DP, _DP, _DP, _DP, _DP, _IP, _IP,
                                           C.POINTER(C.c_longlong), C.c_int]
-            _lib = L
-    return _lib
+            _libs[model] = L
+    return _libs[model]
+
+
+def _L(p: Dict):
+    return lib(model_of(p))
 
 
 def _d(a: np.ndarray):
@@ -153,9 +183,9 @@ def make_params(p: Dict) -> Params:
         setattr(s, k, int(p[k]))
     for k, n in (("g_I", 3), ("J_B", 3), ("r_T_B", 3), ("z_f", 15), ("P_x", 15), ("P_u", 7)):
         arr = getattr(s, k)
-        for i in range(n):
+        for i in range(min(n, len(p[k]))):  # state vectors hold the model's NX entries
             arr[i] = float(p[k][i])
-    for i in range(15):
+    for i in range(len(p["fix_f"])):
         s.fix_f[i] = int(p["fix_f"][i])
     s.soc_thrust = int(p.get("soc_thrust", 0))
     s.glide_slope = int(p.get("glide_slope", 0))
@@ -170,39 +200,39 @@ def make_params(p: Dict) -> Params:
 # ---------------------------------------------------------------------------
 
 def F(p, x, u):
-    out = np.zeros(14)
-    lib().orc_F(C.byref(make_params(p)), _d(np.ascontiguousarray(x, np.float64)),
+    out = np.zeros(nx_of(p) - 1)
+    _L(p).orc_F(C.byref(make_params(p)), _d(np.ascontiguousarray(x, np.float64)),
                 _d(np.ascontiguousarray(u, np.float64)), _d(out))
     return out
 
 
 def g(p, x, u):
     out = np.zeros(10)
-    n = lib().orc_g(C.byref(make_params(p)), _d(np.ascontiguousarray(x, np.float64)),
+    n = _L(p).orc_g(C.byref(make_params(p)), _d(np.ascontiguousarray(x, np.float64)),
                     _d(np.ascontiguousarray(u, np.float64)), _d(out))
     return out[:n]
 
 
 def f(p, x, u):
-    out = np.zeros(NX)
-    lib().orc_f(C.byref(make_params(p)), _d(np.ascontiguousarray(x, np.float64)),
+    out = np.zeros(nx_of(p))
+    _L(p).orc_f(C.byref(make_params(p)), _d(np.ascontiguousarray(x, np.float64)),
                 _d(np.ascontiguousarray(u, np.float64)), _d(out))
     return out
 
 
 def jac(p, x, u):
-    nu = int(p["nu"])
+    nu, NX = int(p["nu"]), nx_of(p)
     A = np.zeros((NX, NX))
     B = np.zeros((NX, nu))
-    lib().orc_jac(C.byref(make_params(p)), _d(np.ascontiguousarray(x, np.float64)),
+    _L(p).orc_jac(C.byref(make_params(p)), _d(np.ascontiguousarray(x, np.float64)),
                   _d(np.ascontiguousarray(u, np.float64)), _d(A), _d(B))
     return A, B
 
 
 def flow(p, xk, uk, uk1, nsub):
     """RK4 flow of Eq. sys-dyn-dil-aug over a unit tau interval (nsub substeps)."""
-    out = np.zeros(NX)
-    lib().orc_flow(C.byref(make_params(p)), _d(np.ascontiguousarray(xk, np.float64)),
+    out = np.zeros(nx_of(p))
+    _L(p).orc_flow(C.byref(make_params(p)), _d(np.ascontiguousarray(xk, np.float64)),
                    _d(np.ascontiguousarray(uk, np.float64)), _d(np.ascontiguousarray(uk1, np.float64)),
                    int(nsub), _d(out))
     return out
@@ -211,12 +241,12 @@ def flow(p, xk, uk, uk1, nsub):
 def discretize(p, X, U):
     X = np.ascontiguousarray(X, np.float64)
     U = np.ascontiguousarray(U, np.float64)
-    N, nu = X.shape[0], int(p["nu"])
+    N, nu, NX = X.shape[0], int(p["nu"]), nx_of(p)
     A = np.zeros((N - 1, NX, NX))
     Bm = np.zeros((N - 1, NX, nu))
     Bp = np.zeros((N - 1, NX, nu))
     xp = np.zeros((N - 1, NX))
-    lib().orc_discretize(C.byref(make_params(p)), N, _d(X), _d(U), _d(A), _d(Bm), _d(Bp), _d(xp))
+    _L(p).orc_discretize(C.byref(make_params(p)), N, _d(X), _d(U), _d(A), _d(Bm), _d(Bp), _d(xp))
     return A, Bm, Bp, xp
 
 
@@ -227,8 +257,9 @@ def discretize(p, X, U):
 class QPData:
     """Scaled subproblem data (Eq. cvx-subproblem-custom) held in numpy arrays."""
 
-    def __init__(self, N: int, nu: int):
-        self.N, self.nu = N, nu
+    def __init__(self, N: int, nu: int, model: str = "6dof"):
+        self.N, self.nu, self.model = N, nu, model
+        NX = NXS[model]
         self.Am = np.zeros((N - 1, NX, NX))
         self.Ap = np.zeros((N - 1, NX, NX))
         self.Bm = np.zeros((N - 1, NX, nu))
@@ -251,7 +282,7 @@ class QPData:
         q.N, q.nu = self.N, self.nu
         for k in ("Am", "Ap", "Bm", "Bp", "w", "eps", "umin", "umax"):
             setattr(q, k, _d(getattr(self, k)))
-        for i in range(NX):
+        for i in range(NXS[self.model]):
             q.zi[i] = self.zi[i]
             q.zf[i] = self.zf[i]
             q.fixf[i] = int(self.fixf[i])
@@ -263,10 +294,11 @@ class QPData:
         return q
 
     def pull(self, q: QP):
-        self.zi[:] = list(q.zi)
-        self.zf[:] = list(q.zf)
-        self.fixf[:] = list(q.fixf)
-        self.ecost[:] = list(q.ecost)
+        n = NXS[self.model]
+        self.zi[:] = list(q.zi)[:n]
+        self.zf[:] = list(q.zf)[:n]
+        self.fixf[:] = list(q.fixf)[:n]
+        self.ecost[:] = list(q.ecost)[:n]
         self.w_cost, self.w_prox, self.w_ep = q.w_cost, q.w_prox, q.w_ep
         self.soc = q.soc
         self.soc_Tmax, self.soc_tan, self.soc_PT = q.soc_Tmax, q.soc_tan, q.soc_PT
@@ -275,8 +307,9 @@ class QPData:
 class PDState:
     """Primal-dual PIPG state (x_hat, u_hat, mu+, mu-, phi, theta)."""
 
-    def __init__(self, N: int, nu: int):
-        self.N, self.nu = N, nu
+    def __init__(self, N: int, nu: int, model: str = "6dof"):
+        self.N, self.nu, self.model = N, nu, model
+        NX = NXS[model]
         self.xh = np.zeros((N, NX))
         self.uh = np.zeros((N, nu))
         self.mup = np.zeros((N - 1, NX))
@@ -291,7 +324,7 @@ class PDState:
         return s
 
     def copy(self) -> "PDState":
-        o = PDState(self.N, self.nu)
+        o = PDState(self.N, self.nu, self.model)
         for k in ("xh", "uh", "mup", "mum", "phi", "th"):
             getattr(o, k)[...] = getattr(self, k)
         return o
@@ -299,9 +332,9 @@ class PDState:
 
 def scale(p, x0, X, U, A, Bm, Bp, xp) -> QPData:
     N, nu = X.shape[0], int(p["nu"])
-    qp = QPData(N, nu)
+    qp = QPData(N, nu, model_of(p))
     qs = qp.cstruct()
-    lib().orc_scale(C.byref(make_params(p)), N, _d(np.ascontiguousarray(x0, np.float64)),
+    _L(p).orc_scale(C.byref(make_params(p)), N, _d(np.ascontiguousarray(x0, np.float64)),
                     _d(np.ascontiguousarray(X, np.float64)), _d(np.ascontiguousarray(U, np.float64)),
                     _d(np.ascontiguousarray(A)), _d(np.ascontiguousarray(Bm)),
                     _d(np.ascontiguousarray(Bp)), _d(np.ascontiguousarray(xp)), C.byref(qs))
@@ -313,7 +346,7 @@ def power(p, qp: QPData, start: PDState, force_iters: int = 0):
     it = C.c_int(0)
     qs = qp.cstruct()
     ss = start.cstruct()
-    sig = lib().orc_power(C.byref(make_params(p)), C.byref(qs), C.byref(ss), int(force_iters), C.byref(it))
+    sig = _L(p).orc_power(C.byref(make_params(p)), C.byref(qs), C.byref(ss), int(force_iters), C.byref(it))
     return sig, it.value
 
 
@@ -321,38 +354,38 @@ def pipgc(p, qp: QPData, sigma: float, ws: PDState, force_iters: int = 0) -> int
     """Runs Alg. PIPG_custom in place on ws; returns the iteration count."""
     qs = qp.cstruct()
     ss = ws.cstruct()
-    return lib().orc_pipgc(C.byref(make_params(p)), C.byref(qs), float(sigma), C.byref(ss), int(force_iters))
+    return _L(p).orc_pipgc(C.byref(make_params(p)), C.byref(qs), float(sigma), C.byref(ss), int(force_iters))
 
 
-def qp_dim(N, nu):
-    return lib().orc_qp_dim(int(N), int(nu))
+def qp_dim(N, nu, model: str = "6dof"):
+    return lib(model).orc_qp_dim(int(N), int(nu))
 
 
 def qp_dense(qp: QPData):
-    N, nu = qp.N, qp.nu
-    nz = qp_dim(N, nu)
+    N, nu, NX = qp.N, qp.nu, NXS[qp.model]
+    nz = qp_dim(N, nu, qp.model)
     P = np.zeros((nz, nz)); pv = np.zeros(nz)
     G = np.zeros((NX * (N - 1), nz)); gv = np.zeros(NX * (N - 1))
     H = np.zeros((N - 1, nz)); hv = np.zeros(N - 1)
     lo = np.zeros(nz); hi = np.zeros(nz)
     qs = qp.cstruct()
-    lib().orc_qp_dense(C.byref(qs), _d(P), _d(pv), _d(G), _d(gv), _d(H), _d(hv), _d(lo), _d(hi))
+    lib(qp.model).orc_qp_dense(C.byref(qs), _d(P), _d(pv), _d(G), _d(gv), _d(H), _d(hv), _d(lo), _d(hi))
     return dict(P=P, p=pv, G=G, g=gv, H=H, h=hv, lo=lo, hi=hi)
 
 
 def z_pack(qp: QPData, s: PDState) -> np.ndarray:
-    z = np.zeros(qp_dim(qp.N, qp.nu))
+    z = np.zeros(qp_dim(qp.N, qp.nu, qp.model))
     qs = qp.cstruct()
     ss = s.cstruct()
-    lib().orc_z_pack(C.byref(qs), C.byref(ss), _d(z))
+    lib(qp.model).orc_z_pack(C.byref(qs), C.byref(ss), _d(z))
     return z
 
 
 def pipg_generic(qp: QPData, alpha, omega, rho, jmax, z1, eta1, chi1):
-    nz = qp_dim(qp.N, qp.nu)
-    z = np.zeros(nz); w = np.zeros(NX * (qp.N - 1)); v = np.zeros(qp.N - 1)
+    nz = qp_dim(qp.N, qp.nu, qp.model)
+    z = np.zeros(nz); w = np.zeros(NXS[qp.model] * (qp.N - 1)); v = np.zeros(qp.N - 1)
     qs = qp.cstruct()
-    lib().orc_pipg_generic(C.byref(qs), float(alpha), float(omega), float(rho), int(jmax),
+    lib(qp.model).orc_pipg_generic(C.byref(qs), float(alpha), float(omega), float(rho), int(jmax),
                            _d(np.ascontiguousarray(z1, np.float64)), _d(np.ascontiguousarray(eta1, np.float64)),
                            _d(np.ascontiguousarray(chi1, np.float64)), _d(z), _d(w), _d(v))
     return z, w, v
@@ -370,9 +403,9 @@ def sym_eig_max(M: np.ndarray) -> float:
 
 
 def init_guess(p, N, x0):
-    nu = int(p["nu"])
+    nu, NX = int(p["nu"]), nx_of(p)
     X = np.zeros((N, NX)); U = np.zeros((N, nu))
-    lib().orc_init_guess(C.byref(make_params(p)), int(N), _d(np.ascontiguousarray(x0, np.float64)), _d(X), _d(U))
+    _L(p).orc_init_guess(C.byref(make_params(p)), int(N), _d(np.ascontiguousarray(x0, np.float64)), _d(X), _d(U))
     return X, U
 
 
@@ -380,7 +413,7 @@ def scp_iterate(p, x0, X, U, ws: PDState, force_pow=0, force_pipg=0, force_sigma
     """One SCP iteration in place on (X, U, ws)."""
     sig = C.c_double(); pit = C.c_int(); jit = C.c_int(); dfc = C.c_double(); stp = C.c_double()
     ss = ws.cstruct()
-    lib().orc_scp_iterate(C.byref(make_params(p)), X.shape[0], _d(np.ascontiguousarray(x0, np.float64)),
+    _L(p).orc_scp_iterate(C.byref(make_params(p)), X.shape[0], _d(np.ascontiguousarray(x0, np.float64)),
                           _d(X), _d(U), C.byref(ss), int(force_pow), int(force_pipg), float(force_sigma),
                           C.byref(sig), C.byref(pit), C.byref(jit), C.byref(dfc), C.byref(stp))
     return dict(sigma=sig.value, pow_iters=pit.value, pipg_iters=jit.value, defect=dfc.value, step=stp.value)
@@ -389,7 +422,7 @@ def scp_iterate(p, x0, X, U, ws: PDState, force_pow=0, force_pipg=0, force_sigma
 def touchdown(p, X, U):
     """Touchdown error of a trajectory (see orc_touchdown)."""
     X = np.ascontiguousarray(X, np.float64); U = np.ascontiguousarray(U, np.float64)
-    return lib().orc_touchdown(C.byref(make_params(p)), X.shape[0], _d(X), _d(U))
+    return _L(p).orc_touchdown(C.byref(make_params(p)), X.shape[0], _d(X), _d(U))
 
 
 def final_iteration_state(p, N, x0, trace, scp_iters):
@@ -398,7 +431,7 @@ def final_iteration_state(p, N, x0, trace, scp_iters):
     iteration, and that iteration's sigma and PIPG count."""
     nu = int(p["nu"])
     X, U = init_guess(p, N, x0)
-    ws = PDState(N, nu)
+    ws = PDState(N, nu, model_of(p))
     for j in range(scp_iters - 1):
         scp_iterate(p, x0, X, U, ws, force_pow=int(trace[j][0]), force_pipg=int(trace[j][1]))
     A, Bm, Bp, xp = discretize(p, X, U)
@@ -411,7 +444,7 @@ def final_iteration_outputs(p, x0, X, U, ws: PDState, sigma, n_pipg):
     """The last SCP iteration as a function of x0 (the reference's first node
     moving with it): returns (fuel, touchdown error) of its updated trajectory."""
     X = X.copy(); U = U.copy(); w = ws.copy()
-    X[0, :14] = x0
+    X[0, :nx_of(p) - 1] = x0
     scp_iterate(p, x0, X, U, w, force_pow=1, force_pipg=n_pipg, force_sigma=sigma)
     return X[0, 0] - X[-1, 0], touchdown(p, X, U)
 
@@ -419,12 +452,12 @@ def final_iteration_outputs(p, x0, X, U, ws: PDState, sigma, n_pipg):
 def solve(p, N, x0, trace: Optional[np.ndarray] = None, replay_scp: int = 0):
     """Full SCP solve of one instance.  With replay_scp > 0, trace[j] = (power
     iterations, PIPG iterations) of SCP iteration j is replayed exactly."""
-    nu = int(p["nu"])
+    nu, NX = int(p["nu"]), nx_of(p)
     X = np.zeros((N, NX)); U = np.zeros((N, nu))
     res = Result()
     jm = max(int(p["scp_jmax"]), int(replay_scp))
     tr = np.zeros((jm, 2), np.int32) if trace is None else np.ascontiguousarray(trace, np.int32)
-    lib().orc_solve(C.byref(make_params(p)), int(N), _d(np.ascontiguousarray(x0, np.float64)), _d(X), _d(U),
+    _L(p).orc_solve(C.byref(make_params(p)), int(N), _d(np.ascontiguousarray(x0, np.float64)), _d(X), _d(U),
                     C.byref(res), _i(tr), 1 if replay_scp > 0 else 0, int(replay_scp))
     return dict(X=X, U=U, tf=res.tf, fuel=res.fuel, status=res.status, scp_iters=res.scp_iters,
                 pipg_iters=res.pipg_iters, pow_iters=res.pow_iters, defect=res.defect, step=res.step,
@@ -436,10 +469,10 @@ def solve_batch(p, x0s, Ns, Nmax=None, nthreads=0):
     B = x0s.shape[0]
     Ns = np.ascontiguousarray(Ns, np.int32)
     Nmax = int(Nmax or Ns.max())
-    nu = int(p["nu"])
+    nu, NX = int(p["nu"]), nx_of(p)
     X = np.zeros((B, Nmax, NX)); U = np.zeros((B, Nmax, nu))
     tf = np.zeros(B); fuel = np.zeros(B)
     st = np.zeros(B, np.int32); sc = np.zeros(B, np.int32); pi = np.zeros(B, np.int64)
-    lib().orc_solve_batch(C.byref(make_params(p)), B, Nmax, _i(Ns), _d(x0s), _d(X), _d(U), _d(tf), _d(fuel),
+    _L(p).orc_solve_batch(C.byref(make_params(p)), B, Nmax, _i(Ns), _d(x0s), _d(X), _d(U), _d(tf), _d(fuel),
                           _i(st), _i(sc), pi.ctypes.data_as(C.POINTER(C.c_longlong)), int(nthreads))
     return dict(X=X, U=U, tf=tf, fuel=fuel, status=st, scp_iters=sc, pipg_iters=pi)
