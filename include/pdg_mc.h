@@ -10,12 +10,28 @@
  * step size by the customized power iteration (Alg. power) and solves the
  * subproblem by customized PIPG (Alg. PIPG_custom with Alg. stopping).
  *
+ * Models.  The problem template of Sec. 2 (dynamics F, path constraints g,
+ * boundary conditions, Mayer cost) is instantiated by a model fixed when the
+ * library is compiled, and every entry point below has the same meaning in
+ * each library:
+ *   libpdg_mc.so       the 6-DoF model of Sec. 5, state size NX = 15;
+ *   libpdg_mc_3dof.so  the translational 3-DoF model, NX = 8: the 6-DoF model
+ *                      without attitude, thrust in the inertial frame, nu = 4,
+ *                      path rows m_dry, altitude, v_max, thrust pointing within
+ *                      delta_max of the up axis, T_min/T_max, optional glide
+ *                      slope.  J_B, r_T_B, theta_max, omega_max and gamma_max
+ *                      are not read.
+ * pdg_mc_model_nx() returns the library's NX.
+ *
  * Conventions
  *   - Layouts are row-major, double precision, instance-major:
- *       x0[B][14]            (m_wet, r[3], v[3], q[4] scalar first, w[3])
- *       X[B][n_max][15]      (m, r, v, q, w, y); y is the CTCS integrator
+ *       x0[B][NX-1]          6-DoF: (m_wet, r[3], v[3], q[4] scalar first, w[3]);
+ *                            3-DoF: (m_wet, r[3], v[3])
+ *       X[B][n_max][NX]      6-DoF: (m, r, v, q, w, y); 3-DoF: (m, r, v, y);
+ *                            y is the CTCS integrator
  *       U[B][n_max][nu]      (T[3], s) for nu = 4; (T[3], gamma[3], s) for nu = 7
- *     Rows k >= n_nodes[b] of X and U are written as zero.
+ *     Rows k >= n_nodes[b] of X and U are written as zero.  Arrays of
+ *     pdg_params indexed like x hold 15 entries; a library reads its first NX.
  *   - Pointers named "device" must point to device memory of the current
  *     device; the caller owns every buffer it passes.  The handle owns its
  *     workspace (allocated by pdg_mc_init and grown on demand).
@@ -97,7 +113,7 @@ void pdg_mc_destroy(pdg_handle* h);
 const char* pdg_mc_last_error(const pdg_handle* h);
 
 /* Solve B instances (Sec. 2.3 SCP loop; all of Sec. 2.3.1-3 per iteration).
- *   x0        device [B][14]
+ *   x0        device [B][NX-1]
  *   n_nodes   device [B] (2..n_max) or NULL for n_max everywhere
  *   mode      0: plain form, one launch per phase per SCP iteration, the
  *                iteration captured once in a CUDA graph and replayed;
@@ -129,10 +145,10 @@ int pdg_mc_solve_batch_host(pdg_handle* h, int B, const double* x0, const int* n
 
 /* Scaled subproblem data about a reference (X, U) (Sec. 2.3.1 STM IVP by RK4
  * with rk4_substeps substeps per interval, then the prescaling of Sec. 2.3.2):
- *   Am  device [B][n_max-1][15][15]   hat A^-_k = P_x^-1 A_k P_x
- *   Bm  device [B][n_max-1][15][nu]   hat B^-_k = P_x^-1 B^-_k P_u
- *   Bp  device [B][n_max-1][15][nu]   hat B^+_k
- *   w   device [B][n_max-1][15]       hat w_k = P_x^-1 (xbar^k(tau_{k+1}) - xbar_{k+1})
+ *   Am  device [B][n_max-1][NX][NX]   hat A^-_k = P_x^-1 A_k P_x
+ *   Bm  device [B][n_max-1][NX][nu]   hat B^-_k = P_x^-1 B^-_k P_u
+ *   Bp  device [B][n_max-1][NX][nu]   hat B^+_k
+ *   w   device [B][n_max-1][NX]       hat w_k = P_x^-1 (xbar^k(tau_{k+1}) - xbar_{k+1})
  * Inputs x0, n_nodes, X, U as above (device).  Rows past n_nodes-1 are zero. */
 int pdg_mc_subproblem(pdg_handle* h, int B, const double* x0, const int* n_nodes,
                       const double* X, const double* U,
@@ -141,8 +157,8 @@ int pdg_mc_subproblem(pdg_handle* h, int B, const double* x0, const int* n_nodes
 /* One SCP iteration in place (plain-form kernels): discretize and scale about
  * (X, U), power iteration, PIPG_custom warm-started from (xh, uh, mup, mum,
  * phi, th), then X += P_x xh, U += P_u uh.  Device buffers:
- *   X [B][n_max][15], U [B][n_max][nu]         reference in / updated out
- *   xh [B][n_max][15], uh [B][n_max][nu], mup, mum, phi [B][n_max-1][15],
+ *   X [B][n_max][NX], U [B][n_max][nu]         reference in / updated out
+ *   xh [B][n_max][NX], uh [B][n_max][nu], mup, mum, phi [B][n_max-1][NX],
  *   th [B][n_max-1]                             warm start in / solution out
  *   force [B][2] (power, PIPG) iteration counts to run exactly, or NULL
  *   sigma [B], defect [B] (max |hat w|), step [B] (max |xh|, |uh|) outputs
@@ -163,7 +179,7 @@ int pdg_mc_scp_step(pdg_handle* h, int B, const double* x0, const int* n_nodes,
  * in the forward pass).  The paper has no gradient; this definition is the
  * solver's own.  Device buffers:
  *   dL_dfuel, dL_dtouch [B]  upstream cotangents (NULL = zero)
- *   grad_x0 [B][14]          d L / d (m_wet, r, v, q, w), with
+ *   grad_x0 [B][NX-1]        d L / d x0 (6-DoF: m_wet, r, v, q, w), with
  *                            L = dL_dfuel fuel + dL_dtouch touchdown
  *   fuel [B], touch [B]      outputs (NULL = not written): fuel = m_1 - m_N and
  *                            touchdown = 0.5 sum_{E_f} ((x_prop,N - z_f)/P_x)^2,
@@ -188,7 +204,7 @@ int pdg_mc_set_threads(pdg_handle* h, int threads);
 
 /* Autotune the launch shape for this handle's n_max, nu and precision on a
  * caller batch (no counterpart in the paper).  Times one solve of the batch
- * (device x0 [B][14], n_nodes as in pdg_mc_solve_batch, execution mode 0/1/2)
+ * (device x0 [B][NX-1], n_nodes as in pdg_mc_solve_batch, execution mode 0/1/2)
  * for every candidate: PIPG form 1 at 128..512 threads and form 2 from the
  * threads it needs up to its limit, multiples of 32; candidates that do not
  * fit on an SM are skipped.  Each candidate runs one untimed solve, then one
@@ -208,7 +224,7 @@ int pdg_mc_autotune(pdg_handle* h, int B, const double* x0, const int* n_nodes, 
  *   form 2: every thread keeps its block rows/columns and iterate entries in
  *           registers for the whole loop; only the vectors exchanged between
  *           the primal and dual steps go through shared memory.  Needs
- *           round32(15 (N-1)) + round32(N G) threads, G = 4 (nu = 4) or 8,
+ *           round32(NX (N-1)) + round32(N G) threads, G = 4 (nu = 4) or 8,
  *           at most 576 (FP32) or 512 (FP64);
  *   form 0: automatic (default) -- form 2 for FP32 when it fits, else form 1.
  * Returns PDG_EINVAL for another value.  Synchronous; no device work. */
@@ -253,6 +269,11 @@ int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream);
  * for 1 and 32 lanes show a pipe whose cost is per warp instruction (GB300's
  * FP64 pipe).  PDG_EINVAL for other arguments.  Synchronizes the stream. */
 int pdg_mc_probe_fma_lanes(int precision, int active_lanes, double* ms, void* cuda_stream);
+
+/* State size NX of the library's model (15: 6-DoF of Sec. 5; 8: 3-DoF).
+ * Needs no device and no handle; the binding checks it against the model it
+ * expects before any call. */
+int pdg_mc_model_nx(void);
 
 #ifdef __cplusplus
 }

@@ -11,7 +11,7 @@
 //     L = dL_dfuel * (m_1 - m_N) + dL_dtouch * 0.5 sum_{E_f} ((x_prop,N - z_f) / P_x)^2
 // of the updated trajectory, x_prop,N being the RK4 propagation of its last
 // interval.  x0 reaches L (i) through the discretization of the first
-// interval (forward mode: dual numbers over the 14 directions of x0 through
+// interval (forward mode: dual numbers over the NX - 1 directions of x0 through
 // the same model code), (ii) through the final PIPG loop (reverse mode,
 // unrolled, recomputed from checkpoints every 50 iterations, projections
 // masked as in the forward pass), (iii) directly through x_1 = x0.
@@ -44,42 +44,6 @@ __device__ __forceinline__ bool operator<(Dual a, Dual b) { return a.v < b.v; }
 __device__ __forceinline__ Dual sqrt(Dual a) {
   const double s = ::sqrt(a.v);
   return Dual(s, s > 0.0 ? 0.5 * a.d / s : 0.0);
-}
-
-// xb += (df/dx)^T v, ub += (df/du)^T v from a compact stage buffer (the
-// transpose of model_jvp).
-template <int NU>
-__device__ __forceinline__ void model_vjp(const double* A, const double* Bd, const double* v, double* xb, double* ub) {
-  xb[4] += A[0] * v[1]; xb[5] += A[0] * v[2]; xb[6] += A[0] * v[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    xb[0] += A[1 + i] * v[4 + i];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) xb[7 + j] += A[4 + 4 * i + j] * v[4 + i];
-  }
-  const double hw0 = A[16], hw1 = A[17], hw2 = A[18], hq0 = A[19], hq1 = A[20], hq2 = A[21], hq3 = A[22];
-  const double v7 = v[7], v8 = v[8], v9 = v[9], v10 = v[10];
-  xb[7] += hw0 * v8 + hw1 * v9 + hw2 * v10;
-  xb[8] += -hw0 * v7 - hw2 * v9 + hw1 * v10;
-  xb[9] += -hw1 * v7 + hw2 * v8 - hw0 * v10;
-  xb[10] += -hw2 * v7 - hw1 * v8 + hw0 * v9;
-  xb[11] += -hq1 * v7 + hq0 * v8 + hq3 * v9 - hq2 * v10;
-  xb[12] += -hq2 * v7 - hq3 * v8 + hq0 * v9 + hq1 * v10;
-  xb[13] += -hq3 * v7 + hq2 * v8 - hq1 * v9 + hq0 * v10;
-  xb[12] += A[23] * v[11]; xb[13] += A[24] * v[11];
-  xb[11] += A[25] * v[12]; xb[13] += A[26] * v[12];
-  xb[11] += A[27] * v[13]; xb[12] += A[28] * v[13];
-  xb[0] += A[29] * v[14]; xb[1] += A[30] * v[14]; xb[2] += A[39] * v[14]; xb[3] += A[40] * v[14];
-  xb[4] += A[31] * v[14]; xb[5] += A[32] * v[14]; xb[6] += A[33] * v[14];
-  xb[9] += A[34] * v[14]; xb[10] += A[35] * v[14];
-  xb[11] += A[36] * v[14]; xb[12] += A[37] * v[14]; xb[13] += A[38] * v[14];
-#pragma unroll
-  for (int c = 0; c < NU; ++c) {
-    double a = 0;
-#pragma unroll
-    for (int i = 0; i < NX; ++i) a += Bd[i * NU + c] * v[i];
-    ub[c] += a;
-  }
 }
 
 // Scratch of the gradient kernel, appended after the solve layout.
@@ -234,7 +198,7 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
 // state) goes from iteration j+1 to iteration j; the intermediates of
 // iteration j must be in place (grad_pipg_iter with update = false on S_j).
 // last: iteration j produced the output (x_hat, u_hat) whose cotangents are in
-// A.xob / A.uob.  Threads 0..14 accumulate the cotangents of the first
+// A.xob / A.uob.  Threads 0..NX-1 accumulate the cotangents of the first
 // interval's blocks hat A^-_1, hat B^-_1, hat B^+_1, hat w_1 in cA/cBm/cBp/cw.
 template <int NU>
 __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& A, double* sm, double alpha,
@@ -378,7 +342,7 @@ __device__ double touchdown_and_reverse(const DParams& P, const Lay& L, const Ad
   const int N = L.N, nsub = P.nsub;
   const double* Xo = sm + A.Xo;
   const double* Uo = sm + A.Uo;
-  double* stg = sm + A.td;                    // stage inputs [nsub][4][15]
+  double* stg = sm + A.td;                    // stage inputs [nsub][4][NX]
   double* buf = sm + A.td + 4 * 32 * NX;     // one stage buffer
   const double h = 1.0 / (double(N - 1) * nsub), h2 = 0.5 * h, h6 = h / 6.0;
   const double* ua = Uo + (N - 2) * NU;
@@ -434,7 +398,7 @@ __device__ double touchdown_and_reverse(const DParams& P, const Lay& L, const Ad
   }
   // x_{N-1} = Xbar_{N-1} + P_x x_hat_{N-1}; the first node is x0 itself
   if (N - 2 == 0) {
-    for (int i = 0; i < 14; ++i) gdir[i] += xb[i];
+    for (int i = 0; i < NX - 1; ++i) gdir[i] += xb[i];
   } else {
     for (int i = 0; i < NX; ++i) sm[A.xob + (N - 2) * NX + i] += P.Px[i] * xb[i];
   }
@@ -446,9 +410,9 @@ __device__ double touchdown_and_reverse(const DParams& P, const Lay& L, const Ad
 }
 
 // Forward-mode derivative of the first interval's discretization (A_1,
-// B^-_1, B^+_1, x_prop,1) along the 14 directions of Xbar_1 = x0, contracted
+// B^-_1, B^+_1, x_prop,1) along the NX - 1 directions of Xbar_1 = x0, contracted
 // with their cotangents (cA, cBm, cBp in unscaled units, cw for x_prop):
-// adds sum cot * d(block)/dx0_j to gacc[j].  Groups of (15 + 2 nu + 1)
+// adds sum cot * d(block)/dx0_j to gacc[j].  Groups of (NX + 2 nu + 1)
 // threads each integrate one direction with dual numbers through the same
 // model code as the solve.
 template <int NU>
@@ -468,9 +432,9 @@ __device__ void tangent_first_interval(const DParams& P, const Lay& L, const Adj
   Dual* xS = xA + NX;
   const double h = 1.0 / (double(N - 1) * nsub), h2 = 0.5 * h, h6 = h / 6.0;
   const double* Ub = sm + L.Ub;
-  for (int d0 = 0; d0 < 14; d0 += groups) {
+  for (int d0 = 0; d0 < NX - 1; d0 += groups) {
     const int j = d0 + g;
-    const bool active = g < groups && j < 14;
+    const bool active = g < groups && j < NX - 1;
     Dual Pv[NX], Sv[NX], Ac[NX];
     if (active) {
       if (evaluator) {

@@ -1,5 +1,7 @@
 // pdg_mc.cu -- kernels and C ABI of the batched GB300 solver for Monte Carlo
-// 6-DoF powered-descent guidance (arXiv 2404.18034).  See include/pdg_mc.h.
+// powered-descent guidance (arXiv 2404.18034).  See include/pdg_mc.h.  The
+// model (6-DoF of Sec. 5, or 3-DoF with PDG_MODEL_3DOF) is fixed at compile
+// time by pdg_device.cuh; nothing in this file depends on which.
 //
 // Two execution forms share the device phases of pdg_phases.cuh:
 //  * persistent: one launch; each CTA takes instance ids from a global work
@@ -66,7 +68,7 @@ __device__ __forceinline__ void copy_s2g(R* dst, const R* src, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-// Load x0 of instance b into the image (x0[14], y = 0); returns false when it
+// Load x0 of instance b into the image (x0[NX-1], y = 0); returns false when it
 // is not finite.  Every thread returns the same value.
 template <typename R>
 __device__ bool load_x0(const Lay& L, R* sm, const double* __restrict__ x0, int b) {
@@ -74,7 +76,7 @@ __device__ bool load_x0(const Lay& L, R* sm, const double* __restrict__ x0, int 
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   if (threadIdx.x < 16) {
-    double v = threadIdx.x < 14 ? x0[(size_t)b * 14 + threadIdx.x] : 0.0;
+    double v = threadIdx.x < NX - 1 ? x0[(size_t)b * (NX - 1) + threadIdx.x] : 0.0;
     if (!isfinite(v)) atomicOr(&bad, 1);
     sm[L.x0 + threadIdx.x] = R(v);
   }
@@ -417,7 +419,7 @@ __global__ void k_pack(int B, int Nmax, int threads, const double* __restrict__ 
     }
   }
   if (dir == 0) {
-    for (int t = threadIdx.x; t < 16; t += blockDim.x) img[L.x0 + t] = t < 14 ? R(x0[(size_t)b * 14 + t]) : R(0);
+    for (int t = threadIdx.x; t < 16; t += blockDim.x) img[L.x0 + t] = t < NX - 1 ? R(x0[(size_t)b * (NX - 1) + t]) : R(0);
     if (threadIdx.x == 0) W.st[b] = ST_RUNNING;
   } else if (threadIdx.x == 0) {
     sigma[b] = double(img[L.sc + 0]);
@@ -442,7 +444,7 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
   const int N = Ns ? Ns[b] : Nmax;
   const int st = status[b];
   if (N < 2 || N > Nmax || !(st == PDG_CONVERGED || st == PDG_MAX_SCP)) {
-    if (threadIdx.x < 14) grad[(size_t)b * 14 + threadIdx.x] = 0.0;
+    if (threadIdx.x < NX - 1) grad[(size_t)b * (NX - 1) + threadIdx.x] = 0.0;
     if (threadIdx.x == 0) {
       if (fuel_out) fuel_out[b] = 0.0;
       if (touch_out) touch_out[b] = 0.0;
@@ -499,13 +501,13 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
   for (int t = threadIdx.x; t < N * NU; t += blockDim.x) sm[AL.Uo + t] = sm[L.Ub + t] + P.Pu[t % NU] * sm[L.uh + t];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double gdir[14];
-    for (int i = 0; i < 14; ++i) gdir[i] = 0.0;
+    double gdir[NX - 1];
+    for (int i = 0; i < NX - 1; ++i) gdir[i] = 0.0;
     const double fu = sm[AL.Xo + IM] - sm[AL.Xo + (N - 1) * NX + IM];
     gdir[IM] += gf;                                      // m_1 = m_wet
     sm[AL.xob + (N - 1) * NX + IM] += -gf * P.Px[IM];    // m_N through x_hat_N
     const double e = touchdown_and_reverse<NU>(P, L, AL, sm, gt, gdir);
-    for (int i = 0; i < 14; ++i) sm[AL.gacc + i] = gdir[i];
+    for (int i = 0; i < NX - 1; ++i) sm[AL.gacc + i] = gdir[i];
     if (fuel_out) fuel_out[b] = fu;
     if (touch_out) touch_out[b] = e;
   }
@@ -543,7 +545,7 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
   __syncthreads();
   tangent_first_interval<NU>(P, L, AL, sm);
   __syncthreads();
-  if (threadIdx.x < 14) grad[(size_t)b * 14 + threadIdx.x] = sm[AL.gacc + threadIdx.x];
+  if (threadIdx.x < NX - 1) grad[(size_t)b * (NX - 1) + threadIdx.x] = sm[AL.gacc + threadIdx.x];
 }
 
 
@@ -653,13 +655,17 @@ static int fail(pdg_handle* h, int code, const std::string& msg) {
 
 static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
   memset(d, 0, sizeof *d);
-  if (!(p->nu == 4 || p->nu == 7)) { *why = "nu must be 4 or 7"; return false; }
+  if (!(p->nu == 4 || p->nu == PDG_MODEL_NU_ALT)) {
+    *why = PDG_MODEL_NU_ALT == 7 ? "nu must be 4 or 7" : "nu must be 4 (this model has no RCS torque)"; return false;
+  }
   if (!(p->precision == 0 || p->precision == 1)) { *why = "precision must be 0 (FP64) or 1 (FP32)"; return false; }
   if (p->rk4_substeps < 1 || p->pipg_jmax < 1 || p->pipg_jcheck < 1 || p->pow_jmax < 1 || p->scp_jmax < 1) {
     *why = "iteration counts and rk4_substeps must be >= 1"; return false;
   }
+#ifndef PDG_MODEL_3DOF
   for (int i = 0; i < 3; ++i) if (!(p->J_B[i] > 0)) { *why = "J_B must be positive"; return false; }
-  for (int i = 0; i < 15; ++i) if (!(p->P_x[i] > 0)) { *why = "P_x must be positive"; return false; }
+#endif
+  for (int i = 0; i < NX; ++i) if (!(p->P_x[i] > 0)) { *why = "P_x must be positive"; return false; }
   for (int i = 0; i < 3; ++i) if (!(p->P_u[i] > 0)) { *why = "P_u must be positive"; return false; }
   if (p->nu == 7) for (int i = 3; i < 6; ++i) if (!(p->P_u[i] > 0)) { *why = "P_u must be positive"; return false; }
   if (!(p->P_u[p->nu - 1] > 0)) { *why = "P_u must be positive"; return false; }
@@ -670,12 +676,12 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
   d->pipg_jcheck = p->pipg_jcheck;
   d->pow_jmax = p->pow_jmax;
   d->scp_jmax = p->scp_jmax;
-  for (int i = 0; i < 15; ++i) d->fix_f[i] = p->fix_f[i] ? 1 : 0;
+  for (int i = 0; i < NX; ++i) d->fix_f[i] = p->fix_f[i] ? 1 : 0;
   d->alpha_mdot = p->alpha_mdot;
   for (int i = 0; i < 3; ++i) {
     d->g[i] = p->g_I[i];
     d->J[i] = p->J_B[i];
-    d->Jinv[i] = 1.0 / p->J_B[i];
+    d->Jinv[i] = p->J_B[i] > 0 ? 1.0 / p->J_B[i] : 0.0;  // the 3-DoF model has no inertia
     d->rT[i] = p->r_T_B[i];
   }
   d->m_dry = p->m_dry;
@@ -688,7 +694,7 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
   d->gamma_max2 = p->gamma_max * p->gamma_max;
   d->s_min = p->s_min;
   d->s_max = p->s_max;
-  for (int i = 0; i < 15; ++i) {
+  for (int i = 0; i < NX; ++i) {
     d->z_f[i] = p->z_f[i];
     d->Px[i] = p->P_x[i];
     d->Pxinv[i] = 1.0 / p->P_x[i];
@@ -737,10 +743,10 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
 // shared memory, half of that (more CTAs per SM keep the FP64 pipe busier).
 // Within [128, 512].
 static int threads_for(int N, int nu, int precision) {
-  int t = round32((N - 1) * 15) + 32;
+  int t = round32((N - 1) * NX) + 32;
   if (precision == 0) {
     const Lay L = make_lay(N, nu, t);
-    if ((size_t)L.total * 8 * 3 <= 227 * 1024) t = round32(round32((N - 1) * 15) / 2) + 32;
+    if ((size_t)L.total * 8 * 3 <= 227 * 1024) t = round32(round32((N - 1) * NX) / 2) + 32;
   }
   if (t > 512) t = 512;
   if (t < 128) t = 128;
@@ -1167,8 +1173,8 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
 
 #define PDG_DISPATCH(h, fn, ...)                                         \
   ((h)->p.precision == 0                                                 \
-       ? ((h)->p.nu == 4 ? fn<double, 4>(__VA_ARGS__) : fn<double, 7>(__VA_ARGS__)) \
-       : ((h)->p.nu == 4 ? fn<float, 4>(__VA_ARGS__) : fn<float, 7>(__VA_ARGS__)))
+       ? ((h)->p.nu == 4 ? fn<double, 4>(__VA_ARGS__) : fn<double, PDG_MODEL_NU_ALT>(__VA_ARGS__)) \
+       : ((h)->p.nu == 4 ? fn<float, 4>(__VA_ARGS__) : fn<float, PDG_MODEL_NU_ALT>(__VA_ARGS__)))
 
 extern "C" {
 
@@ -1243,7 +1249,7 @@ int pdg_mc_solve_batch_host(pdg_handle* h, int B, const double* x0, const int* n
   if (!x0 || !X || !U || !tf || !fuel || !status || !scp_iters || !pipg_iters) return fail(h, PDG_EINVAL, "NULL buffer");
   PDG_CUDA(h, cudaSetDevice(h->device));
   const int nu = h->p.nu, Nm = h->n_max;
-  const size_t bx0 = sizeof(double) * 14 * B, bN = sizeof(int) * B, bX = sizeof(double) * (size_t)B * Nm * 15,
+  const size_t bx0 = sizeof(double) * (NX - 1) * B, bN = sizeof(int) * B, bX = sizeof(double) * (size_t)B * Nm * NX,
                bU = sizeof(double) * (size_t)B * Nm * nu, bs = sizeof(double) * B, bi = sizeof(int) * B,
                bl = sizeof(long long) * B;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -1440,7 +1446,7 @@ int pdg_mc_grad_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes
   PDG_CUDA(h, cudaSetDevice(h->device));
   cudaStream_t s = (cudaStream_t)cuda_stream;
   return h->p.nu == 4 ? run_grad<4>(h, B, x0, n_nodes, dL_dfuel, dL_dtouch, grad_x0, fuel, touch, status, s)
-                      : run_grad<7>(h, B, x0, n_nodes, dL_dfuel, dL_dtouch, grad_x0, fuel, touch, status, s);
+                      : run_grad<PDG_MODEL_NU_ALT>(h, B, x0, n_nodes, dL_dfuel, dL_dtouch, grad_x0, fuel, touch, status, s);
 }
 
 static int probe_fma_run(int precision, int active, double* best_ms, long long* lane_fma, void* cuda_stream) {
@@ -1484,6 +1490,8 @@ int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream) {
   *tflops = 2.0 * (double)n / (ms * 1e-3) / 1e12;
   return PDG_OK;
 }
+
+int pdg_mc_model_nx(void) { return NX; }
 
 int pdg_mc_probe_fma_lanes(int precision, int active_lanes, double* ms, void* cuda_stream) {
   if (!ms || (precision != 0 && precision != 1) || active_lanes < 1 || active_lanes > 32) return PDG_EINVAL;

@@ -11,48 +11,13 @@ namespace pdg {
 __device__ __forceinline__ double max0(double x) { return __double_as_longlong(x) < 0 ? 0.0 : x; }
 __device__ __forceinline__ float max0(float x) { return __float_as_int(x) < 0 ? 0.0f : x; }
 
-// Initial guess (the paper asks for "an appropriate" one; Sec. 5): straight
-// lines in r, v, w from x0 to z_f, normalized linear interpolation of q, mass
-// from m_wet to (m_wet + m_dry)/2, y = 0, hover thrust m|g| along body x,
-// gamma = 0, s = tf_guess.
+// Initial guess of every node (Sec. 5 asks for "an appropriate" one; the
+// model's model_init_node says which).
 template <typename R, int NU>
 __device__ void phase_init_guess(const DParams& P, const Lay& L, R* sm) {
   const int N = L.N;
-  const R* x0 = sm + L.x0;
-  R* Xb = sm + L.Xb;
-  R* Ub = sm + L.Ub;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    const R t = R(k) / R(N - 1);
-    const R a = R(1) - t;
-    R* x = Xb + k * NX;
-    const R mf = R(0.5) * (x0[IM] + R(P.m_dry));
-    x[IM] = a * x0[IM] + t * mf;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      x[IR + i] = a * x0[IR + i] + t * R(P.z_f[IR + i]);
-      x[IV + i] = a * x0[IV + i] + t * R(P.z_f[IV + i]);
-      x[IW + i] = a * x0[IW + i] + t * R(P.z_f[IW + i]);
-    }
-    R dq = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) dq += x0[IQ + i] * R(P.z_f[IQ + i]);
-    const R sg = dq < R(0) ? R(-1) : R(1);
-    R qq[4], n2 = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      qq[i] = a * x0[IQ + i] + t * sg * R(P.z_f[IQ + i]);
-      n2 += qq[i] * qq[i];
-    }
-    const R inq = R(1) / sqrt(n2);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) x[IQ + i] = qq[i] * inq;
-    x[IY] = 0;
-    R* u = Ub + k * NU;
-#pragma unroll
-    for (int c = 0; c < NU; ++c) u[c] = 0;
-    u[0] = x[IM] * R(P.g0);
-    u[NU - 1] = R(P.tf_guess);
-  }
+  for (int k = threadIdx.x; k < N; k += blockDim.x)
+    model_init_node<R, NU>(P, sm + L.x0, R(k) / R(N - 1), sm + L.Xb + k * NX, sm + L.Ub + k * NU);
 }
 
 // Sec. 2.3.1 + 2.3.2: integrate, on every interval, the joint IVP of x and its
@@ -631,8 +596,8 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
 // Exchanged through shared memory: the relaxed dual phi~ and the per-node
 // difference of the relaxed CTCS duals (td, as in phase_pipg) read by the
 // primal step, and the extrapolated primal (2 z_{j+1} - z~_j) read by the
-// dual step; node vectors are padded to 16 entries so they load as 16-byte
-// vectors.
+// dual step; node vectors are padded to NXS entries (a multiple of four) so
+// they load as 16-byte vectors.
 // Needs blockDim.x >= pipg_reg_threads(N, NU).
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int pipg_reg_groups(int nu) { return nu <= 4 ? 4 : 8; }
@@ -657,14 +622,15 @@ template <> struct Vec16B<double> {
 };
 
 // Shared-memory offsets of the exchange vectors (inside the phase-local union
-// region, 16-byte aligned): vp[(N-1)][16], dx[N][16], du[N][NUP], td[N].
+// region, 16-byte aligned): vp[(N-1)][NXS], dx[N][NXS], du[N][NUP], td[N].
+constexpr int NXS = (NX + 3) & ~3;
 struct RegLay { int vp, dx, du, td, end; };
 __host__ __device__ inline RegLay make_reg_lay(const Lay& L) {
   const int nup = L.nu <= 4 ? 4 : 8;
   RegLay Q;
   int o = (L.xt + 3) & ~3;
-  Q.vp = o; o += (L.N - 1) * 16;
-  Q.dx = o; o += L.N * 16;
+  Q.vp = o; o += (L.N - 1) * NXS;
+  Q.dx = o; o += L.N * NXS;
   Q.du = o; o += L.N * nup;
   Q.td = o; o += (L.N + 3) & ~3;  // CTCS-dual difference per node (as in phase_pipg)
   Q.end = o;
@@ -672,13 +638,13 @@ __host__ __device__ inline RegLay make_reg_lay(const Lay& L) {
 }
 
 // g + sum_{r < NX} a[r] v[r] with v read from shared memory in 16-byte pieces
-// (four interleaved accumulators; v is 16-byte aligned, v[15] is padding)
+// (four interleaved accumulators; v is 16-byte aligned, v[NX..NXS) is padding)
 template <typename R>
-__device__ __forceinline__ R dot15_sm(const R (&a)[NX], const R* v, R g) {
+__device__ __forceinline__ R dotx_sm(const R (&a)[NX], const R* v, R g) {
   constexpr int W = Vec16B<R>::n;
   R h[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int q = 0; q < 16; q += W) {
+  for (int q = 0; q < NXS; q += W) {
     R c[W];
     Vec16B<R>::ld(v + q, c);
 #pragma unroll
@@ -767,7 +733,7 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
     r4 = sm[L.mup + tid]; r2 = r4 - aw;
     r5 = sm[L.mum + tid]; r3 = r5 - aw;
     r7 = r6 = sm[L.phi + tid];
-    vp[kd * 16 + i] = r6;
+    vp[kd * NXS + i] = r6;
   }
   if (has_u) {
     r0 = r1 = sm[L.uh + ku * NU + cc];
@@ -800,10 +766,10 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
     // ---- projected gradient step (primal)
     if (has_d) {
       // branch-free (see phase_pipg): zero column for the last node
-      const R G = dot15_sm(a1, vp + km * 16, fma(s_iy, tds[kx], -vp[kd * 16 + i]));
+      const R G = dotx_sm(a1, vp + km * NXS, fma(s_iy, tds[kx], -vp[kd * NXS + i]));
       R xn = fma(-alpha, G, fma(c1, r0, cost));
       xn = (last_x && P.fix_f[i]) ? sm[L.zf + i] : xn;
-      dxs[kx * 16 + i] = fma(R(2), xn, -r0);
+      dxs[kx * NXS + i] = fma(R(2), xn, -r0);
       r0 += rho * (xn - r0);
       if constexpr (chk) { zn = umax(zn, OB::abs(xn)); zo = umax(zo, OB::abs(r1)); zd = umax(zd, OB::abs(xn - r1)); }
       r1 = xn;
@@ -811,8 +777,8 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
       R un = 0;
       if (has_u) {
         R Gs = 0;
-        if (ku <= N - 2) Gs = dot15_sm(a1, vp + ku * 16, Gs);
-        if (ku >= 1) Gs = dot15_sm(a2, vp + (ku - 1) * 16, Gs);
+        if (ku <= N - 2) Gs = dotx_sm(a1, vp + ku * NXS, Gs);
+        if (ku >= 1) Gs = dotx_sm(a2, vp + (ku - 1) * NXS, Gs);
         un = c1 * r0 - alpha * Gs;
         if (cc == NU - 1) un = rmin(rmax(un, r2), r3);
       }
@@ -865,8 +831,8 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
       }
       r4 = mp;
       r5 = mm;
-      R r = r8 + (fma(R(2), mp, -a) - fma(R(2), mm, -b)) - dxs[kx * 16 + i];
-      r = dot15_sm(a2, dxs + kd * 16, r);
+      R r = r8 + (fma(R(2), mp, -a) - fma(R(2), mm, -b)) - dxs[kx * NXS + i];
+      r = dotx_sm(a2, dxs + kd * NXS, r);
       R r2b = 0;
 #pragma unroll
       for (int c0 = 0; c0 < NU; c0 += Vec16B<R>::n) {
@@ -883,10 +849,10 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
       r6 += rb * r;  // = phi~ + rho (phi_new - phi~)
       if constexpr (chk) { rn = umax(rn, OB::abs(pn)); ro = umax(ro, OB::abs(r7)); rd = umax(rd, OB::abs(pn - r7)); }
       r7 = pn;
-      vp[kd * 16 + i] = r6;
+      vp[kd * NXS + i] = r6;
     } else if (th_warp) {
       if (has_th) {
-        const R hy = dxs[(v + 1) * 16 + IY] - dxs[v * 16 + IY] - r7;
+        const R hy = dxs[(v + 1) * NXS + IY] - dxs[v * NXS + IY] - r7;
         const R tn = max0(r5 + beta * hy);
         r5 += rho * (tn - r5);
         if constexpr (chk) { rn = umax(rn, OB::nonneg(tn)); ro = umax(ro, OB::abs(r6)); rd = umax(rd, OB::abs(tn - r6)); }

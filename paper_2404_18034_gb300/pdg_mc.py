@@ -1,6 +1,7 @@
 """Python binding of the C ABI in include/pdg_mc.h (ctypes; marshalling only).
 
-Every computation runs in the CUDA library libpdg_mc.so; there is no fallback.
+Every computation runs in the CUDA library of the parameter dict's model
+(libpdg_mc.so: 6-DoF; libpdg_mc_3dof.so: 3-DoF); there is no fallback.
 Importing this module does not touch the GPU; creating a Solver loads the
 library and raises if it is missing or no CUDA device is usable.  Device
 buffers are torch CUDA tensors (float64 / int32 / int64), host buffers numpy
@@ -16,7 +17,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("PDG_MC_LIB", os.path.join(HERE, "libpdg_mc.so"))
-NX = 15
+LIB_PATHS = {"6dof": LIB_PATH, "3dof": os.path.join(HERE, "libpdg_mc_3dof.so")}
+NXS = {"6dof": 15, "3dof": 8}
+NX = NXS["6dof"]
 
 PDG_CONVERGED, PDG_MAX_SCP, PDG_NONFINITE, PDG_BUDGET, PDG_BAD_INPUT = 0, 1, 2, 3, 4
 ERRORS = {-1: "PDG_EINVAL", -2: "PDG_ENOMEM", -3: "PDG_ECUDA"}
@@ -24,7 +27,7 @@ EXPORTS = ("pdg_mc_init", "pdg_mc_destroy", "pdg_mc_last_error", "pdg_mc_solve_b
            "pdg_mc_solve_batch_host", "pdg_mc_subproblem", "pdg_mc_scp_step", "pdg_mc_launch_info",
            "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc",
            "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form", "pdg_mc_probe_fma_lanes",
-           "pdg_mc_autotune")
+           "pdg_mc_autotune", "pdg_mc_model_nx")
 
 
 class PdgParams(C.Structure):
@@ -53,17 +56,30 @@ class PdgParams(C.Structure):
 
 
 _VP = C.c_void_p
-_lib = None
+_libs: Dict = {}
 
 
-def load_library(path: str = LIB_PATH):
-    """Load libpdg_mc.so; raises RuntimeError when it has not been built."""
-    global _lib
-    if _lib is not None:
-        return _lib
+def model_of(p: Dict) -> str:
+    m = p.get("model", "6dof")
+    if m not in NXS:
+        raise ValueError(f"unknown model {m!r}")
+    return m
+
+
+def load_library(path: Optional[str] = None, model: str = "6dof"):
+    """Load the model's library (libpdg_mc.so for 6-DoF, libpdg_mc_3dof.so for
+    3-DoF, or `path`); raises RuntimeError when it has not been built or its
+    state size is not the model's."""
+    path = path or LIB_PATHS[model]
+    if (path, model) in _libs:
+        return _libs[(path, model)]
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} (run paper_2404_18034_gb300.build.build())")
     L = C.CDLL(path)
+    L.pdg_mc_model_nx.argtypes = []
+    L.pdg_mc_model_nx.restype = C.c_int
+    if L.pdg_mc_model_nx() != NXS[model]:
+        raise RuntimeError(f"{path} implements NX = {L.pdg_mc_model_nx()}, not the {model} model")
     L.pdg_mc_init.argtypes = [C.POINTER(PdgParams), C.c_int, C.POINTER(_VP)]
     L.pdg_mc_destroy.argtypes = [_VP]
     L.pdg_mc_destroy.restype = None
@@ -88,7 +104,7 @@ def load_library(path: str = LIB_PATH):
                  "pdg_mc_solve_batch_noalloc", "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form",
                  "pdg_mc_probe_fma_lanes", "pdg_mc_autotune"):
         getattr(L, name).restype = C.c_int
-    _lib = L
+    _libs[(path, model)] = L
     return L
 
 
@@ -105,9 +121,9 @@ def make_params(p: Dict, precision: int = 0, budget_seconds: float = 0.0) -> Pdg
         setattr(s, k, int(p[k]))
     for k, n in (("g_I", 3), ("J_B", 3), ("r_T_B", 3), ("z_f", 15), ("P_x", 15), ("P_u", 7)):
         arr = getattr(s, k)
-        for i in range(n):
+        for i in range(min(n, len(p[k]))):  # state vectors hold the model's NX entries
             arr[i] = float(p[k][i])
-    for i in range(15):
+    for i in range(len(p["fix_f"])):
         s.fix_f[i] = int(p["fix_f"][i])
     s.budget_seconds = float(budget_seconds)
     s.soc_thrust = int(p.get("soc_thrust", 0))
@@ -160,7 +176,9 @@ class Solver:
 
     def __init__(self, params: Dict, n_max: int, precision: int = 0, budget_seconds: float = 0.0,
                  tune_cache: Optional[str] = None, mode: int = 1):
-        self.lib = load_library()
+        self.model = model_of(params)
+        self.nx = NXS[self.model]
+        self.lib = load_library(model=self.model)
         self.params = params
         self.nu = int(params["nu"])
         self.n_max = int(n_max)
@@ -177,7 +195,8 @@ class Solver:
             import torch
 
             from .autotune import lookup
-            e = lookup(torch.cuda.get_device_name(), self.n_max, self.nu, self.precision, mode, tune_cache)
+            e = lookup(torch.cuda.get_device_name(), self.n_max, self.nu, self.precision, mode, tune_cache,
+                       self.model)
             if e:
                 self.set_pipg_form(e[1])
                 self.set_threads(e[0])
@@ -208,7 +227,7 @@ class Solver:
     def alloc_outputs(self, B: int, device="cuda"):
         import torch
         f = dict(dtype=torch.float64, device=device)
-        return dict(X=torch.empty(B, self.n_max, NX, **f), U=torch.empty(B, self.n_max, self.nu, **f),
+        return dict(X=torch.empty(B, self.n_max, self.nx, **f), U=torch.empty(B, self.n_max, self.nu, **f),
                     tf=torch.empty(B, **f), fuel=torch.empty(B, **f),
                     status=torch.empty(B, dtype=torch.int32, device=device),
                     scp_iters=torch.empty(B, dtype=torch.int32, device=device),
@@ -243,11 +262,11 @@ class Solver:
         return out
 
     def grad(self, x0, n_nodes=None, dL_dfuel=None, dL_dtouch=None, stream=None):
-        """pdg_mc_grad_batch: returns grad (B x 14), fuel, touch, status."""
+        """pdg_mc_grad_batch: returns grad (B x NX-1), fuel, touch, status."""
         import torch
         B = int(x0.shape[0])
         f = dict(dtype=torch.float64, device=x0.device)
-        o = dict(grad=torch.empty(B, 14, **f), fuel=torch.empty(B, **f), touch=torch.empty(B, **f),
+        o = dict(grad=torch.empty(B, self.nx - 1, **f), fuel=torch.empty(B, **f), touch=torch.empty(B, **f),
                  status=torch.empty(B, dtype=torch.int32, device=x0.device))
         rc = self.lib.pdg_mc_grad_batch(self.h, B, _ptr(x0), _ptr(n_nodes), _ptr(dL_dfuel), _ptr(dL_dtouch),
                                         _ptr(o["grad"]), _ptr(o["fuel"]), _ptr(o["touch"]), _ptr(o["status"]),
@@ -262,7 +281,7 @@ class Solver:
         B = x0.shape[0]
         if n_nodes is not None:
             n_nodes = np.ascontiguousarray(n_nodes, np.int32)
-        out = out or dict(X=np.empty((B, self.n_max, NX)), U=np.empty((B, self.n_max, self.nu)),
+        out = out or dict(X=np.empty((B, self.n_max, self.nx)), U=np.empty((B, self.n_max, self.nu)),
                           tf=np.empty(B), fuel=np.empty(B), status=np.empty(B, np.int32),
                           scp_iters=np.empty(B, np.int32), pipg_iters=np.empty(B, np.int64))
         rc = self.lib.pdg_mc_solve_batch_host(self.h, B, _np(x0), _np(n_nodes), int(mode), _np(out["X"]),
@@ -277,8 +296,9 @@ class Solver:
         B = int(x0.shape[0])
         f = dict(dtype=torch.float64, device=x0.device)
         nm = self.n_max - 1
-        o = dict(Am=torch.empty(B, nm, NX, NX, **f), Bm=torch.empty(B, nm, NX, self.nu, **f),
-                 Bp=torch.empty(B, nm, NX, self.nu, **f), w=torch.empty(B, nm, NX, **f))
+        nx = self.nx
+        o = dict(Am=torch.empty(B, nm, nx, nx, **f), Bm=torch.empty(B, nm, nx, self.nu, **f),
+                 Bp=torch.empty(B, nm, nx, self.nu, **f), w=torch.empty(B, nm, nx, **f))
         rc = self.lib.pdg_mc_subproblem(self.h, B, _ptr(x0), _ptr(n_nodes), _ptr(X), _ptr(U), _ptr(o["Am"]),
                                         _ptr(o["Bm"]), _ptr(o["Bp"]), _ptr(o["w"]), self._stream(stream))
         self._check(rc, "pdg_mc_subproblem")

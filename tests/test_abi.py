@@ -57,10 +57,29 @@ def test_init_rejects_bad_arguments(lib, params):
 
 def test_binding_fails_loudly_without_library(tmp_path):
     from paper_2404_18034_gb300 import pdg_mc
-    saved = pdg_mc._lib
-    pdg_mc._lib = None
-    try:
-        with pytest.raises(RuntimeError, match="not built"):
-            pdg_mc.load_library(str(tmp_path / "missing.so"))
-    finally:
-        pdg_mc._lib = saved
+    with pytest.raises(RuntimeError, match="not built"):
+        pdg_mc.load_library(str(tmp_path / "missing.so"))
+
+
+def test_3dof_library_exports_and_checks(lib, inputs):
+    """The 3-DoF model's library exports the same entry points, reports its
+    state size, and rejects nu = 7 (the model has no RCS torque) and a
+    non-positive P_x entry among its 8 states; the binding refuses to load a
+    library under the wrong model."""
+    from paper_2404_18034_gb300 import pdg_mc
+    L3 = pdg_mc.load_library(model="3dof")
+    assert lib.pdg_mc_model_nx() == 15 and L3.pdg_mc_model_nx() == 8
+    for name in pdg_mc.EXPORTS:
+        assert hasattr(L3, name), name
+    p3 = inputs.load_params(model="3dof")
+    h = C.c_void_p()
+    p = pdg_mc.make_params(p3)
+    p.nu = 7
+    assert L3.pdg_mc_init(C.byref(p), 10, C.byref(h)) == -1
+    assert b"nu must be 4" in L3.pdg_mc_last_error(None)
+    p = pdg_mc.make_params(p3)
+    p.P_x[7] = 0.0
+    assert L3.pdg_mc_init(C.byref(p), 10, C.byref(h)) == -1
+    assert b"P_x" in L3.pdg_mc_last_error(None)
+    with pytest.raises(RuntimeError, match="not the 3dof model"):
+        pdg_mc.load_library(pdg_mc.LIB_PATHS["6dof"], model="3dof")

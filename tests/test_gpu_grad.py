@@ -18,9 +18,10 @@ def torch_cuda():
 
 
 def _fd(oracle, p, x0, X, U, ws, sig, n, h=1e-6):
-    g = np.zeros((14, 2))
-    for j in range(14):
-        e = np.zeros(14); e[j] = h
+    d = len(x0)
+    g = np.zeros((d, 2))
+    for j in range(d):
+        e = np.zeros(d); e[j] = h
         fp = np.array(oracle.final_iteration_outputs(p, x0 + e, X, U, ws, sig, n))
         fm = np.array(oracle.final_iteration_outputs(p, x0 - e, X, U, ws, sig, n))
         g[j] = (fp - fm) / (2 * h)
@@ -28,11 +29,16 @@ def _fd(oracle, p, x0, X, U, ws, sig, n, h=1e-6):
 
 
 @pytest.mark.parametrize("nu,N,B,ov", [(4, 15, 6, {}), (4, 10, 3, {}), (7, 12, 2, {}),
-                                        (4, 12, 3, {"glide_slope": 1, "dt_min": 0.3, "dt_max": 0.55})])
+                                        (4, 12, 3, {"glide_slope": 1, "dt_min": 0.3, "dt_max": 0.55}),
+                                        (4, 15, 4, {"model": "3dof"}),
+                                        (4, 11, 3, {"model": "3dof", "glide_slope": 1})])
 def test_gradient_matches_oracle_finite_differences(torch_cuda, oracle, inputs, nu, N, B, ov):
+    """Both models: the 6-DoF one of Sec. 5 and the 3-DoF instance of the
+    template (gradient d L / d (m_wet, r, v) there)."""
     torch = torch_cuda
     from paper_2404_18034_gb300.pdg_mc import Solver
-    p = inputs.load_params(nu=nu, **ov)
+    ov = dict(ov)
+    p = inputs.load_params(nu=nu, model=ov.pop("model", None), **ov)
     S = Solver(p, N)
     x0 = inputs.dispersion(p, B, inputs.config_seed(3), "bj")
     d = torch.from_numpy(x0).cuda()
