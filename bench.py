@@ -1,5 +1,6 @@
 #!/usr/bin/env python
-"""Benchmark: converged 6-DoF powered-descent SCP solves per second on GB300.
+"""Benchmark: converged 6-DoF powered-descent SCP solves per second on GB300
+(--model 3dof: the translational 3-DoF instance of the same problem template).
 
 One step = one full batched solve (every SCP iteration of every instance:
 RK4 discretization with STMs, prescaling, power iteration, PIPG, update) of
@@ -37,7 +38,7 @@ METRIC = "converged PDG SCP solves/s on 1 GB300, batch 16384, N=15; % FP64/FP32 
 PROFILED_TRAFFIC = {
     # ncu (dram__bytes_read.sum, dram__bytes_write.sum) of k_persistent<double,4,1>
     # on 456 instances (one per CTA slot): 12.02 MB read + 67.07 MB written
-    "f9a158eb2633dad0": {("fp64", 4, 15, "persistent"): 79.09e6 / 456},
+    "f9a158eb2633dad0": {("6dof", "fp64", 4, 15, "persistent"): 79.09e6 / 456},
 }
 
 
@@ -66,6 +67,8 @@ def parse():
     ap.add_argument("--nodes", type=int, default=15)
     ap.add_argument("--dispersion", default="bj", choices=["bj", "paper256", "nominal"])
     ap.add_argument("--nu", type=int, default=4, choices=[4, 7], help="7: the paper's model with the RCS torque")
+    ap.add_argument("--model", default="6dof", choices=["6dof", "3dof"],
+                    help="3dof: the translational instance of the problem template (nu = 4)")
     ap.add_argument("--uneven", action="store_true", help="N per instance uniform in {10, 15, 20, 30}")
     ap.add_argument("--grad", action="store_true", help="time gradients (pdg_mc_grad_batch) instead of solves")
     ap.add_argument("--soc", action="store_true",
@@ -106,7 +109,7 @@ def workload_name(a):
     soc = "_soc" if getattr(a, "soc", False) else ""
     gs = "_gs" if getattr(a, "glide_slope", False) else ""
     tb = "_tbounds" if (getattr(a, "dt_min", 0) or getattr(a, "dt_max", 0) or getattr(a, "tf_max", 0)) else ""
-    return f"pdg6dof_{a.dispersion}_B{a.batch}_{n}{nu}{soc}{gs}{tb}_{a.precision}_{a.mode}"
+    return f"pdg{getattr(a, 'model', '6dof')}_{a.dispersion}_B{a.batch}_{n}{nu}{soc}{gs}{tb}_{a.precision}_{a.mode}"
 
 
 class ClockSampler:
@@ -192,7 +195,7 @@ def run_reference(a):
     if rank != 0:
         return
     from paper_2404_18034_gb300 import inputs
-    p = inputs.load_params()
+    p = inputs.load_params(nu=a.nu, model=a.model)
     seed = inputs.config_seed(2)
     x0 = inputs.dispersion(p, a.batch, seed, a.dispersion)
     cores = os.cpu_count() or 1
@@ -228,7 +231,7 @@ def run_grad(a):
     build.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    p = inputs.load_params()
+    p = inputs.load_params(model=a.model)
     x0 = torch.from_numpy(inputs.dispersion(p, a.batch, inputs.config_seed(3), a.dispersion)).to(dev)
     S = Solver(p, a.nodes, 0)
     gf = torch.ones(a.batch, dtype=torch.float64, device=dev)
@@ -253,7 +256,7 @@ def run_grad(a):
             "value": ok / (sum(ms) * 1e-3), "unit": "grads/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"pdg6dof_grad_{a.dispersion}_B{a.batch}_N{a.nodes}_fp64", "batch": a.batch,
+            "config": {"workload": f"pdg{a.model}_grad_{a.dispersion}_B{a.batch}_N{a.nodes}_fp64", "batch": a.batch,
                        "nodes": a.nodes, "l2": "256 MiB buffer written between timed steps",
                        "includes": "the forward solve and the adjoint of its last SCP iteration"},
             "clocks": clk.summary(), "gpu_launches": 2 * a.steps}
@@ -311,8 +314,8 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     prec = 0 if a.precision == "fp64" else 1
-    p = inputs.load_params(nu=a.nu, soc_thrust=int(a.soc), glide_slope=int(a.glide_slope), dt_min=a.dt_min,
-                           dt_max=a.dt_max, tf_max=a.tf_max)
+    p = inputs.load_params(nu=a.nu, model=a.model, soc_thrust=int(a.soc), glide_slope=int(a.glide_slope),
+                           dt_min=a.dt_min, dt_max=a.dt_max, tf_max=a.tf_max)
     seed = shard_seed(inputs.config_seed(2), rank)
     x0h = inputs.dispersion(p, a.batch, seed, a.dispersion)
     x0 = torch.from_numpy(x0h).to(dev)
@@ -368,7 +371,7 @@ def run_ours(a):
 
     # roofline of the dominant kernel (the persistent solve kernel is the whole step)
     fl = flops.solve_flops(Ns_h if a.uneven else np.full(a.batch, a.nodes), p["nu"], p["rk4_substeps"], scp, pow_it,
-                           pipg)
+                           pipg, a.model)
     launch_s = float(np.mean(ms)) * 1e-3
     achieved = fl / launch_s / 1e12
     clocks = clk.summary()
@@ -417,7 +420,8 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": total_ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
             "config": {"workload": workload_name(a), "batch_per_gpu": a.batch, "global_batch": a.batch * world,
-                       "nodes": "uniform in {10,15,20,30}" if a.uneven else a.nodes, "nu": p["nu"], "precision": a.precision, "mode": a.mode,
+                       "nodes": "uniform in {10,15,20,30}" if a.uneven else a.nodes, "model": a.model, "nu": p["nu"],
+                       "precision": a.precision, "mode": a.mode,
                        "dispersion": a.dispersion, "parallelism": f"dp{world}",
                        "l2": "256 MiB buffer written between timed steps",
                        "threads_per_cta": info["threads"], "ctas_per_sm": info["ctas_per_sm"],
@@ -430,8 +434,8 @@ def run_ours(a):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
                          "frac": achieved / peak_nominal,
                          "traffic": (PROFILED_TRAFFIC.get(kernel_source_hash(), {}).get(
-                             (a.precision, p["nu"], a.nodes, a.mode)) or 0) * a.batch or None,
-                         "traffic_algorithmic_bytes": int(x0h.nbytes + a.batch * a.nodes * (15 + p["nu"]) * 8
+                             (a.model, a.precision, p["nu"], a.nodes, a.mode)) or 0) * a.batch or None,
+                         "traffic_algorithmic_bytes": int(x0h.nbytes + a.batch * a.nodes * (S.nx + p["nu"]) * 8
                                                           + a.batch * 28),
                          "kernel": "whole plain-form step" if mode == 0 else "k_persistent",
                          "flops_per_launch": fl,

@@ -15,33 +15,42 @@ of any particular kernel:
   columns through the structural nonzeros of df/dx (62 FMA), the df/du column
   term for the 2 nu control columns (15 FMA), the RK4 stage/accumulate updates
   (3 flops per entry), and one evaluation of f and its Jacobians (250 flops).
+
+The 3-DoF model (NX = 8) has the same structure with its own constants: 13
+structural nonzeros of df/dx in the STM right-hand side and about 100 flops
+per evaluation of f and its Jacobians.
 """
 
-NX = 15
+# model: (NX, structural nonzeros of df/dx used per STM column, flops of one model evaluation)
+MODELS = {"6dof": (15, 62, 250), "3dof": (8, 13, 100)}
+NX = MODELS["6dof"][0]
 
 
-def pipg_iter(N: int, nu: int) -> int:
-    mat = 2 * 2 * (N - 1) * (NX * NX + 2 * NX * nu)
-    vec = 9 * (NX + nu) * N + 9 * 2 * NX * (N - 1) + 8 * (NX + 1) * (N - 1)
+def pipg_iter(N: int, nu: int, model: str = "6dof") -> int:
+    nx = MODELS[model][0]
+    mat = 2 * 2 * (N - 1) * (nx * nx + 2 * nx * nu)
+    vec = 9 * (nx + nu) * N + 9 * 2 * nx * (N - 1) + 8 * (nx + 1) * (N - 1)
     return mat + vec
 
 
-def power_iter(N: int, nu: int) -> int:
-    mat = 2 * 2 * (N - 1) * (NX * NX + 2 * NX * nu)
-    return mat + 2 * ((NX + nu) * N + 2 * NX * (N - 1))
+def power_iter(N: int, nu: int, model: str = "6dof") -> int:
+    nx = MODELS[model][0]
+    mat = 2 * 2 * (N - 1) * (nx * nx + 2 * nx * nu)
+    return mat + 2 * ((nx + nu) * N + 2 * nx * (N - 1))
 
 
-def discretization(N: int, nu: int, nsub: int) -> int:
-    ncol = NX + 2 * nu
-    per_stage = ncol * (2 * 62 + 3 * NX) + 2 * nu * 2 * NX + 250
+def discretization(N: int, nu: int, nsub: int, model: str = "6dof") -> int:
+    nx, nnz, ev = MODELS[model]
+    ncol = nx + 2 * nu
+    per_stage = ncol * (2 * nnz + 3 * nx) + 2 * nu * 2 * nx + ev
     return (N - 1) * nsub * 4 * per_stage
 
 
-def solve_flops(N, nu, nsub, scp_iters, pow_iters, pipg_iters) -> float:
+def solve_flops(N, nu, nsub, scp_iters, pow_iters, pipg_iters, model: str = "6dof") -> float:
     """Total algorithmic flops of a solve given its executed counters (arrays
     over instances are accepted)."""
     import numpy as np
     N = np.asarray(N)
-    return float(np.sum(np.asarray(scp_iters) * np.vectorize(discretization)(N, nu, nsub)
-                        + np.asarray(pow_iters) * np.vectorize(power_iter)(N, nu)
-                        + np.asarray(pipg_iters) * np.vectorize(pipg_iter)(N, nu)))
+    return float(np.sum(np.asarray(scp_iters) * np.vectorize(discretization)(N, nu, nsub, model)
+                        + np.asarray(pow_iters) * np.vectorize(power_iter)(N, nu, model)
+                        + np.asarray(pipg_iters) * np.vectorize(pipg_iter)(N, nu, model)))
