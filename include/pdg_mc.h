@@ -242,7 +242,8 @@ int pdg_mc_pipg_form(const pdg_handle* h);
  * iteration up to scp_jmax is launched (finished instances return at once)
  * and the call never synchronizes the stream.  The per-instance workspace
  * lives in a fixed 32 MiB device array that the library defines, so every
- * GPU that loads the library holds those 32 MiB until the process exits.
+ * GPU that loads the library holds those 32 MiB until the process exits (each
+ * model library has its own array: a process using both holds 64 MiB).
  *   - Batches that need more than the 32 MiB (about 650 instances at
  *     n_max = 15 in FP64, twice that in FP32) are rejected with PDG_EINVAL
  *     and a message that states the limit; nothing is launched.

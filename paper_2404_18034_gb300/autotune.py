@@ -26,7 +26,6 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "autotune_cache.json")
 NXS = {"6dof": 15, "3dof": 8}
-NX = NXS["6dof"]
 SMEM_MAX = 232448
 
 

@@ -23,7 +23,6 @@ per evaluation of f and its Jacobians.
 
 # model: (NX, structural nonzeros of df/dx used per STM column, flops of one model evaluation)
 MODELS = {"6dof": (15, 62, 250), "3dof": (8, 13, 100)}
-NX = MODELS["6dof"][0]
 
 
 def pipg_iter(N: int, nu: int, model: str = "6dof") -> int:

@@ -19,7 +19,6 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("PDG_MC_LIB", os.path.join(HERE, "libpdg_mc.so"))
 LIB_PATHS = {"6dof": LIB_PATH, "3dof": os.path.join(HERE, "libpdg_mc_3dof.so")}
 NXS = {"6dof": 15, "3dof": 8}
-NX = NXS["6dof"]
 
 PDG_CONVERGED, PDG_MAX_SCP, PDG_NONFINITE, PDG_BUDGET, PDG_BAD_INPUT = 0, 1, 2, 3, 4
 ERRORS = {-1: "PDG_EINVAL", -2: "PDG_ENOMEM", -3: "PDG_ECUDA"}

@@ -190,3 +190,32 @@ def test_fp32_tracks_fp64(torch_cuda, inputs):
     rel = ((a["fuel"] - b["fuel"]).abs() / a["fuel"].abs())[ok]
     assert rel.max().item() < 5e-2
     S64.close(); S32.close()
+
+
+def test_edge_cases_and_host_api(torch_cuda, inputs):
+    """Empty batch; out-of-range node counts and non-finite x0 give
+    PDG_BAD_INPUT with zero outputs; N = 2 runs; the host-buffer entry point
+    returns what the device one does."""
+    torch = torch_cuda
+    from paper_2404_18034_gb300.pdg_mc import PDG_BAD_INPUT
+    p, S = _solver(inputs, 12)
+    x0 = inputs.dispersion(p, 5, 1, "bj")
+    x0[3, 2] = np.nan
+    Ns = np.array([2, 1, 13, 12, 5], np.int32)
+    assert S.solve(_d(torch, x0[:0]), mode=1)["X"].shape[0] == 0
+    for mode in (0, 1, 2):
+        out = S.solve(_d(torch, x0), _d(torch, Ns), mode=mode)
+        torch.cuda.synchronize()
+        st = out["status"].cpu().numpy()
+        assert list(st[[1, 2, 3]]) == [PDG_BAD_INPUT] * 3
+        assert st[0] in (0, 1) and st[4] in (0, 1)
+        for b in (1, 2, 3):
+            assert out["X"][b].abs().max().item() == 0.0 and out["tf"][b].item() == 0.0
+    ok = inputs.dispersion(p, 6, 9, "bj")
+    dev = S.solve(_d(torch, ok), mode=1)
+    torch.cuda.synchronize()
+    host = S.solve_host(ok, mode=1)
+    for k in ("X", "U", "tf", "fuel", "status", "scp_iters", "pipg_iters"):
+        np.testing.assert_array_equal(dev[k].cpu().numpy(), host[k])
+    S.close()
+

@@ -34,10 +34,11 @@ def _batch(inputs, p, B, seed):
     return x0, Ns
 
 
-def test_noalloc_matches_regular_solve_on_two_calls(torch_cuda, inputs):
+@pytest.mark.parametrize("model", ["6dof", "3dof"])
+def test_noalloc_matches_regular_solve_on_two_calls(torch_cuda, inputs, model):
     torch = torch_cuda
     from paper_2404_18034_gb300.pdg_mc import Solver
-    p = inputs.load_params()
+    p = inputs.load_params(model=model)
     S = Solver(p, 15)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     for call, (B, seed) in enumerate([(48, 101), (29, 202)]):
