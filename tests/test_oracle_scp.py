@@ -99,3 +99,47 @@ def test_paper_monte_carlo_distribution_converges(oracle, inputs):
     b = oracle.solve_batch(p, x0, np.full(n, 15, np.int32))
     assert int(np.sum(b["status"] == 0)) == mc["runs_converged"], np.bincount(b["status"])
     assert b["scp_iters"].max() <= mc["scp_iteration_limit"]
+
+
+def _pack(X, U, ws):
+    return np.concatenate([X[1:].ravel(), U.ravel(), ws.xh.ravel(), ws.uh.ravel(), ws.mup.ravel(), ws.mum.ravel(),
+                           ws.phi.ravel(), ws.th.ravel()])
+
+
+def _scp_map(O, p, x0, z, X, U, ws, sig, n):
+    """One SCP iteration (sigma and the PIPG count held) as a map of the
+    reference and the warm start, packed as a vector."""
+    X, U, w = X.copy(), U.copy(), ws.copy()
+    o = 0
+    for arr in (X[1:], U, w.xh, w.uh, w.mup, w.mum, w.phi, w.th):
+        arr[...] = z[o:o + arr.size].reshape(arr.shape)
+        o += arr.size
+    O.scp_iterate(p, x0, X, U, w, force_pow=1, force_pipg=n, force_sigma=sig)
+    return _pack(X, U, w)
+
+
+@pytest.mark.parametrize("model,N", [("3dof", 10), ("6dof", 8)])
+def test_scp_map_is_not_contractive_at_convergence(oracle, inputs, model, N):
+    """The total derivative of the converged outputs through the SCP fixed
+    point, lambda = dl/dZ + J_Z^T lambda by sweeps, needs the spectral radius
+    of the SCP map's Jacobian J_Z below one.  At the last iterate of converged
+    solves it is not: central differences of the map (reference and warm
+    start, sigma and the PIPG count held) give rho(J_Z) >= 1, so the sweeps
+    diverge and the exported gradient is that of the last SCP iteration."""
+    p = inputs.load_params(model=model)
+    x0 = inputs.dispersion(p, 1, 3, "bj")[0]
+    r = oracle.solve(p, N, x0)
+    assert r["status"] == 0
+    X, U, ws, sig, n = oracle.final_iteration_state(p, N, x0, r["trace"], r["scp_iters"])
+    z0 = _pack(X, U, ws)
+    nx = len(p["P_x"])
+    scale = np.concatenate([np.tile(p["P_x"], N - 1), np.tile(p["P_u"][:p["nu"]], N),
+                            np.ones(z0.size - (N - 1) * nx - N * p["nu"])])
+    J = np.zeros((z0.size, z0.size))
+    for j in range(z0.size):
+        e = np.zeros(z0.size)
+        e[j] = 1e-6 * scale[j]
+        J[:, j] = (_scp_map(oracle, p, x0, z0 + e, X, U, ws, sig, n)
+                   - _scp_map(oracle, p, x0, z0 - e, X, U, ws, sig, n)) / (2 * e[j])
+    rho = np.abs(np.linalg.eigvals(J * scale[None, :] / scale[:, None])).max()
+    assert rho >= 0.99, rho
