@@ -21,7 +21,10 @@
  *                      delta_max of the up axis, T_min/T_max, optional glide
  *                      slope.  J_B, r_T_B, theta_max, omega_max and gamma_max
  *                      are not read.
- * pdg_mc_model_nx() returns the library's NX.
+ * pdg_mc_model_nx() returns the library's NX.  A library for another model is
+ * built from a user header passed as -DPDG_MODEL_HEADER="<path>" that defines
+ * the same model interface (see csrc/pdg_device.cuh); its constants come in
+ * through pdg_params.model_params.
  *
  * Conventions
  *   - Layouts are row-major, double precision, instance-major:
@@ -96,6 +99,9 @@ typedef struct pdg_params {
   double dt_min, dt_max, tf_max;  /* Sec. 2.2 time bounds, 0 = off: imposed as the node box
                              s_k in [dt_min (N-1), min(dt_max (N-1), tf_max)] on the
                              dilation (sufficient for FOH s) */
+  double model_params[16]; /* constants of a model supplied at build time through
+                             PDG_MODEL_HEADER (read by its device code as P.mp[i]);
+                             the built-in models do not read them */
 } pdg_params;
 
 typedef struct pdg_handle pdg_handle;

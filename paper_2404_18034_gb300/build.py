@@ -3,7 +3,8 @@
 One library per model of the problem template (the model is a compile-time
 choice of csrc/pdg_device.cuh): libpdg_mc.so holds the 6-DoF model of Sec. 5,
 libpdg_mc_3dof.so the translational 3-DoF model.  Both compile from the same
-sources, in parallel.
+sources, in parallel.  build_model() compiles a library for a model header of
+the caller's (the interface is listed in csrc/pdg_device.cuh).
 """
 from __future__ import annotations
 
@@ -54,6 +55,23 @@ def build(force: bool = False, verbose: bool = False, models=("6dof", "3dof")) -
     if failed:
         raise subprocess.CalledProcessError(1, failed[0])
     return LIB
+
+
+def build_model(header: str, out: str, force: bool = False) -> str:
+    """Compile the solver for the model in `header` (passed to the device code
+    as PDG_MODEL_HEADER) into the library `out`; returns `out`.  The header may
+    include the solver's own headers by name (csrc is on the include path)."""
+    header = os.path.abspath(header)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= max(
+            [os.path.getmtime(header)] + [os.path.getmtime(p) for p in _sources()]):
+        return out
+    nvcc = os.environ.get("NVCC", "nvcc")
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = [nvcc, "-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+           "-I", INCLUDE, "-I", SRC, f'-DPDG_MODEL_HEADER="{header}"', os.path.join(SRC, "pdg_mc.cu"), "-o", tmp]
+    subprocess.check_call(cmd)
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

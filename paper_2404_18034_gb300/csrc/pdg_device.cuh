@@ -33,6 +33,7 @@ struct DParams {
   double tan_gs2;    // tan^2(gamma_gs)
   double s_lo, s_hi; // node box on the dilation: [s_min, s_max] tightened by the time bounds,
   double dt_lo, dt_hi;  // of which dt_min, dt_max scale with N - 1 (0 = off)
+  double mp[16];     // constants of a model supplied through PDG_MODEL_HEADER
 };
 
 // Per-instance shared-memory layout (element offsets in units of R).  The
@@ -49,14 +50,34 @@ struct Lay {
 // The model -- F, g, their compact Jacobians and the initial guess of one
 // instance of the problem template of Sec. 2 -- is chosen when the library is
 // compiled: the 6-DoF model of Sec. 5 by default, the translational 3-DoF
-// model with PDG_MODEL_3DOF.  Each model header defines NX, the state indices
-// IM (mass, the cost) and IY (CTCS integrator, last), SA_A, model_eval,
-// model_jvp and model_init_node; the phases use nothing else of the model.
-#ifdef PDG_MODEL_3DOF
+// model with PDG_MODEL_3DOF, or a model of the caller's with
+// PDG_MODEL_HEADER="<path>".  A model header defines, in namespace pdg:
+//   NX          state size; the CTCS integrator y is the last state (IY = NX-1)
+//   IM          index of the mass, whose final value the cost maximizes
+//   IY          NX - 1
+//   SA_A        slots of its compact df/dx
+//   PDG_MODEL_NU_ALT  a second control size it supports besides 4 (else 4)
+//   model_eval<R, NU>(P, x, u, f, A, Bd): f = s (F, sum |g|_+^2), compact
+//               df/dx in A[SA_A], dense df/du in Bd[NX][NU]
+//   model_jvp<R, NU>(A, Bd, S, cu, lam, d): d = (df/dx) S + lam (df/du) e_cu
+//   model_vjp<NU>(A, Bd, v, xb, ub): xb += (df/dx)^T v, ub += (df/du)^T v
+//   model_init_node<R, NU>(P, x0, t, x, u): initial guess at node fraction t
+// with R in {double, float} and, for the gradient, a dual number type.  The
+// phases use nothing else of the model; P.mp holds its own constants.
+#if defined(PDG_MODEL_HEADER)
+#include PDG_MODEL_HEADER
+#elif defined(PDG_MODEL_3DOF)
 #include "pdg_model_3dof.cuh"
 #else
 #include "pdg_model_6dof.cuh"
 #endif
+#ifndef PDG_MODEL_NU_ALT
+#define PDG_MODEL_NU_ALT 4
+#endif
+static_assert(pdg::NX >= 2 && pdg::NX <= pdg::NXMAX, "a model's state size must lie in [2, 15]");
+static_assert(pdg::IY == pdg::NX - 1, "the CTCS integrator must be the last state");
+static_assert(pdg::IM >= 0 && pdg::IM < pdg::NX - 1, "the cost's mass index must be a state of xi");
+static_assert(PDG_MODEL_NU_ALT == 4 || PDG_MODEL_NU_ALT == 7, "controls: nu = 4, optionally nu = 7");
 
 namespace pdg {
 

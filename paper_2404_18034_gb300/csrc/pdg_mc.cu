@@ -729,6 +729,7 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
   d->s_hi = p->tf_max > 0 && p->tf_max < p->s_max ? p->tf_max : p->s_max;
   d->dt_lo = p->dt_min;
   d->dt_hi = p->dt_max;
+  for (int i = 0; i < 16; ++i) d->mp[i] = p->model_params[i];
   d->soc = p->soc_thrust ? 1 : 0;
   d->soc_tan = tan(p->delta_max);
   if (d->soc && !(p->P_u[0] == p->P_u[1] && p->P_u[1] == p->P_u[2])) {

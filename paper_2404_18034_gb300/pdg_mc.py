@@ -51,6 +51,7 @@ class PdgParams(C.Structure):
         ("soc_thrust", C.c_int),
         ("glide_slope", C.c_int), ("gamma_gs", C.c_double),
         ("dt_min", C.c_double), ("dt_max", C.c_double), ("tf_max", C.c_double),
+        ("model_params", C.c_double * 16),
     ]
 
 
@@ -60,7 +61,7 @@ _libs: Dict = {}
 
 def model_of(p: Dict) -> str:
     m = p.get("model", "6dof")
-    if m not in NXS:
+    if m not in NXS and m != "custom":
         raise ValueError(f"unknown model {m!r}")
     return m
 
@@ -68,7 +69,9 @@ def model_of(p: Dict) -> str:
 def load_library(path: Optional[str] = None, model: str = "6dof"):
     """Load the model's library (libpdg_mc.so for 6-DoF, libpdg_mc_3dof.so for
     3-DoF, or `path`); raises RuntimeError when it has not been built or its
-    state size is not the model's."""
+    state size is not the model's.  model="custom" loads a library built
+    from a model header of the caller's (build.build_model) and takes its
+    state size from the library."""
     path = path or LIB_PATHS[model]
     if (path, model) in _libs:
         return _libs[(path, model)]
@@ -77,7 +80,7 @@ def load_library(path: Optional[str] = None, model: str = "6dof"):
     L = C.CDLL(path)
     L.pdg_mc_model_nx.argtypes = []
     L.pdg_mc_model_nx.restype = C.c_int
-    if L.pdg_mc_model_nx() != NXS[model]:
+    if model != "custom" and L.pdg_mc_model_nx() != NXS[model]:
         raise RuntimeError(f"{path} implements NX = {L.pdg_mc_model_nx()}, not the {model} model")
     L.pdg_mc_init.argtypes = [C.POINTER(PdgParams), C.c_int, C.POINTER(_VP)]
     L.pdg_mc_destroy.argtypes = [_VP]
@@ -130,6 +133,8 @@ def make_params(p: Dict, precision: int = 0, budget_seconds: float = 0.0) -> Pdg
     s.gamma_gs = float(p.get("gamma_gs", 0.0))
     for k in ("dt_min", "dt_max", "tf_max"):
         setattr(s, k, float(p.get(k, 0.0)))
+    for i, v in enumerate(p.get("model_params", ())):
+        s.model_params[i] = float(v)
     return s
 
 
@@ -174,10 +179,12 @@ class Solver:
     """Handle on the batched solver (pdg_mc_init / pdg_mc_destroy)."""
 
     def __init__(self, params: Dict, n_max: int, precision: int = 0, budget_seconds: float = 0.0,
-                 tune_cache: Optional[str] = None, mode: int = 1):
+                 tune_cache: Optional[str] = None, mode: int = 1, library: Optional[str] = None):
+        """library: path of a library built from a model header of the
+        caller's (build.build_model); params["model"] is then "custom"."""
         self.model = model_of(params)
-        self.nx = NXS[self.model]
-        self.lib = load_library(model=self.model)
+        self.lib = load_library(library, model=self.model)
+        self.nx = int(self.lib.pdg_mc_model_nx())
         self.params = params
         self.nu = int(params["nu"])
         self.n_max = int(n_max)

@@ -1,0 +1,148 @@
+// pdg_model_3dof_drag.cuh -- a caller-supplied model for the problem template
+// of Sec. 2 of arXiv 2404.18034, compiled into the solver through
+// PDG_MODEL_HEADER by the tests: the 3-DoF powered-descent model with
+// quadratic aerodynamic drag,
+//   m' = -alpha ||T||,  r' = v,  v' = T / m + g - (c_D / m) ||v|| v,
+// c_D = P.mp[0] (pdg_params.model_params[0]).  The path constraints, the
+// initial guess and the boundary conditions are those of the built-in 3-DoF
+// model; with c_D = 0 the two models coincide.
+#pragma once
+
+namespace pdg {
+
+constexpr int NX = 8;
+constexpr int IM = 0, IR = 1, IV = 4, IY = 7;
+// compact df/dx: [0] s (r rows wrt v); [1..3] dvdot/dm; [4..10] y row (m,
+// r_x, v0..2, r_y, r_z); [11] unused; [12..20] dvdot_i/dv_j (drag), row-major
+constexpr int SA_A = 22;
+#define PDG_MODEL_NU_ALT 4
+
+template <typename R, int NU>
+__device__ __forceinline__ void model_eval(const DParams& P, const R* x, const R* u, R* f, R* A, R* Bd) {
+  const R m = x[IM];
+  const R rx = x[IR], ry = x[IR + 1], rz = x[IR + 2];
+  const R v0 = x[IV], v1 = x[IV + 1], v2 = x[IV + 2];
+  const R T0 = u[0], T1 = u[1], T2 = u[2];
+  const R s = u[NU - 1];
+  const R cd = R(P.mp[0]);
+  const R nT = sqrt(T0 * T0 + T1 * T1 + T2 * T2);
+  const R inT = nT > R(0) ? R(1) / nT : R(0);
+  const R t0 = T0 * inT, t1 = T1 * inT, t2 = T2 * inT;
+  const R nv = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+  const R inv = nv > R(0) ? R(1) / nv : R(0);
+  const R im = R(1) / m;
+  const R cdm = cd * im;
+  R F[7];
+  F[0] = -R(P.alpha_mdot) * nT;
+  F[1] = v0; F[2] = v1; F[3] = v2;
+  F[4] = T0 * im + R(P.g[0]) - cdm * nv * v0;
+  F[5] = T1 * im + R(P.g[1]) - cdm * nv * v1;
+  F[6] = T2 * im + R(P.g[2]) - cdm * nv * v2;
+  R gp[7];
+  gp[0] = R(P.m_dry) - m;
+  gp[1] = -rx;
+  gp[2] = v0 * v0 + v1 * v1 + v2 * v2 - R(P.vmax2);
+  gp[3] = nT - T0 * R(P.sec_delta);
+  gp[4] = nT - R(P.T_max);
+  gp[5] = R(P.T_min) - nT;
+  if (P.soc) { gp[3] = R(-1); gp[4] = R(-1); }
+  gp[6] = P.gs ? R(P.tan_gs2) * (ry * ry + rz * rz) - rx * rx : R(-1);
+  R pen = 0;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    gp[i] = gp[i] > R(0) ? gp[i] : R(0);
+    pen += gp[i] * gp[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 7; ++i) f[i] = s * F[i];
+  f[7] = s * pen;
+  const R sim = s * im;
+  // dvdot/dm = -(T - c_D ||v|| v) / m^2
+  A[0] = s;
+  A[1] = -sim * im * (T0 - cd * nv * v0);
+  A[2] = -sim * im * (T1 - cd * nv * v1);
+  A[3] = -sim * im * (T2 - cd * nv * v2);
+  const R s2 = R(2) * s;
+  A[4] = -s2 * gp[0];
+  A[5] = -s2 * (gp[1] + gp[6] * R(2) * rx);
+  A[6] = s2 * gp[2] * R(2) * v0;
+  A[7] = s2 * gp[2] * R(2) * v1;
+  A[8] = s2 * gp[2] * R(2) * v2;
+  A[9] = s2 * gp[6] * R(2) * R(P.tan_gs2) * ry;
+  A[10] = s2 * gp[6] * R(2) * R(P.tan_gs2) * rz;
+  A[11] = 0;
+  // d(-c_D/m ||v|| v)/dv = -(c_D/m) (||v|| I + v v^T / ||v||)
+  const R sc = -s * cdm;
+  const R vv[3] = {v0, v1, v2};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) A[12 + 3 * i + j] = sc * ((i == j ? nv : R(0)) + vv[i] * vv[j] * inv);
+  }
+#pragma unroll
+  for (int i = 0; i < NX * NU; ++i) Bd[i] = R(0);
+  const R sa = -s * R(P.alpha_mdot);
+  Bd[0 * NU + 0] = sa * t0; Bd[0 * NU + 1] = sa * t1; Bd[0 * NU + 2] = sa * t2;
+  Bd[4 * NU + 0] = sim; Bd[5 * NU + 1] = sim; Bd[6 * NU + 2] = sim;
+  const R gt = gp[3] + gp[4] - gp[5];
+  Bd[7 * NU + 0] = s2 * (gt * t0 - gp[3] * R(P.sec_delta));
+  Bd[7 * NU + 1] = s2 * gt * t1;
+  Bd[7 * NU + 2] = s2 * gt * t2;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) Bd[i * NU + NU - 1] = F[i];
+  Bd[7 * NU + NU - 1] = pen;
+}
+
+template <typename R, int NU>
+__device__ __forceinline__ void model_jvp(const R* __restrict__ A, const R* __restrict__ Bd, const R* S,
+                                          int cu, R lam, R* d) {
+  d[0] = R(0);
+  d[1] = A[0] * S[4]; d[2] = A[0] * S[5]; d[3] = A[0] * S[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    d[4 + i] = A[1 + i] * S[0] + A[12 + 3 * i] * S[4] + A[13 + 3 * i] * S[5] + A[14 + 3 * i] * S[6];
+  d[7] = A[4] * S[0] + A[5] * S[1] + A[6] * S[4] + A[7] * S[5] + A[8] * S[6] + A[9] * S[2] + A[10] * S[3];
+  if (cu >= 0) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) d[i] += lam * Bd[i * NU + cu];
+  }
+}
+
+template <int NU>
+__device__ __forceinline__ void model_vjp(const double* A, const double* Bd, const double* v, double* xb, double* ub) {
+  xb[4] += A[0] * v[1]; xb[5] += A[0] * v[2]; xb[6] += A[0] * v[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    xb[0] += A[1 + i] * v[4 + i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) xb[4 + j] += A[12 + 3 * i + j] * v[4 + i];
+  }
+  xb[0] += A[4] * v[7]; xb[1] += A[5] * v[7]; xb[2] += A[9] * v[7]; xb[3] += A[10] * v[7];
+  xb[4] += A[6] * v[7]; xb[5] += A[7] * v[7]; xb[6] += A[8] * v[7];
+#pragma unroll
+  for (int c = 0; c < NU; ++c) {
+    double a = 0;
+#pragma unroll
+    for (int i = 0; i < NX; ++i) a += Bd[i * NU + c] * v[i];
+    ub[c] += a;
+  }
+}
+
+template <typename R, int NU>
+__device__ __forceinline__ void model_init_node(const DParams& P, const R* x0, R t, R* x, R* u) {
+  const R a = R(1) - t;
+  const R mf = R(0.5) * (x0[IM] + R(P.m_dry));
+  x[IM] = a * x0[IM] + t * mf;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    x[IR + i] = a * x0[IR + i] + t * R(P.z_f[IR + i]);
+    x[IV + i] = a * x0[IV + i] + t * R(P.z_f[IV + i]);
+  }
+  x[IY] = 0;
+#pragma unroll
+  for (int c = 0; c < NU; ++c) u[c] = 0;
+  u[0] = x[IM] * R(P.g0);
+  u[NU - 1] = R(P.tf_guess);
+}
+
+}  // namespace pdg
