@@ -1138,11 +1138,6 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
   const size_t need = al(bX) + al(bU) + 2 * al(bB) + 2 * al(bI) + al(bL) + al(bR) + al(bC);
   if (h->gws_bytes < need) {
     if (h->gws) cudaFree(h->gws);
-  if (h->cls) cudaFree(h->cls);
-  for (int i = 0; i <= NMAX; ++i) {
-    if (h->cls_streams[i]) cudaStreamDestroy(h->cls_streams[i]);
-    if (h->cls_events[i]) cudaEventDestroy(h->cls_events[i]);
-  }
     h->gws = nullptr;
     h->gws_bytes = 0;
     PDG_CUDA(h, cudaMalloc(&h->gws, need));
@@ -1257,12 +1252,6 @@ int pdg_mc_solve_batch_host(pdg_handle* h, int B, const double* x0, const int* n
   const size_t need = al(bx0) + al(bN) + al(bX) + al(bU) + 2 * al(bs) + 2 * al(bi) + al(bl);
   if (h->stage_bytes < need) {
     if (h->stage) cudaFree(h->stage);
-  if (h->gws) cudaFree(h->gws);
-  if (h->cls) cudaFree(h->cls);
-  for (int i = 0; i <= NMAX; ++i) {
-    if (h->cls_streams[i]) cudaStreamDestroy(h->cls_streams[i]);
-    if (h->cls_events[i]) cudaEventDestroy(h->cls_events[i]);
-  }
     h->stage = nullptr;
     h->stage_bytes = 0;
     PDG_CUDA(h, cudaMalloc(&h->stage, need));

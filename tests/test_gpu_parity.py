@@ -272,14 +272,28 @@ def test_edge_cases(torch_cuda, inputs):
 
 
 def test_host_api_equals_device_api(torch_cuda, inputs):
+    """The host-buffer entry point returns what the device one does.  The
+    handle's workspaces grow in turn (shape-class streams, host staging,
+    gradient workspace) and each growth must leave the others intact: the
+    solves and the gradient afterwards still agree and close() succeeds."""
     torch = torch_cuda
     p, S = _solver(inputs, 4, 15)
     x0 = inputs.dispersion(p, 6, 9, "bj")
-    dev = S.solve(torch.from_numpy(x0).cuda(), mode=1)
+    d0 = torch.from_numpy(x0).cuda()
+    classed = S.solve(d0, mode=2)
+    dev = S.solve(d0, mode=1)
     torch.cuda.synchronize()
     host = S.solve_host(x0, mode=1)
     for k in ("X", "U", "tf", "fuel", "status", "scp_iters", "pipg_iters"):
         np.testing.assert_array_equal(dev[k].cpu().numpy(), host[k])
+    g = S.grad(d0)
+    again = S.solve(d0, mode=2)
+    host2 = S.solve_host(x0, mode=0)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(again["status"].cpu().numpy(), classed["status"].cpu().numpy())
+    np.testing.assert_array_equal(host2["status"], host["status"])
+    assert np.all(np.isfinite(g["grad"].cpu().numpy()[g["status"].cpu().numpy() <= 1]))
+    S.close()
 
 
 def test_plain_and_persistent_agree(torch_cuda, inputs):
