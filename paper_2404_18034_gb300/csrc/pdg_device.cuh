@@ -57,6 +57,7 @@ struct Lay {
 //   IY          NX - 1
 //   SA_A        slots of its compact df/dx
 //   PDG_MODEL_NU_ALT  a second control size it supports besides 4 (else 4)
+//   PDG_MODEL_USES_INERTIA  defined when the model reads J_B (then checked > 0)
 //   model_eval<R, NU>(P, x, u, f, A, Bd): f = s (F, sum |g|_+^2), compact
 //               df/dx in A[SA_A], dense df/du in Bd[NX][NU]
 //   model_jvp<R, NU>(A, Bd, S, cu, lam, d): d = (df/dx) S + lam (df/du) e_cu

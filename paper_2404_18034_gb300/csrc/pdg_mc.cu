@@ -662,7 +662,7 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
   if (p->rk4_substeps < 1 || p->pipg_jmax < 1 || p->pipg_jcheck < 1 || p->pow_jmax < 1 || p->scp_jmax < 1) {
     *why = "iteration counts and rk4_substeps must be >= 1"; return false;
   }
-#ifndef PDG_MODEL_3DOF
+#ifdef PDG_MODEL_USES_INERTIA
   for (int i = 0; i < 3; ++i) if (!(p->J_B[i] > 0)) { *why = "J_B must be positive"; return false; }
 #endif
   for (int i = 0; i < NX; ++i) if (!(p->P_x[i] > 0)) { *why = "P_x must be positive"; return false; }

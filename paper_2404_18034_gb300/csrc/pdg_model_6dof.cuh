@@ -11,8 +11,9 @@ constexpr int NX = 15;
 constexpr int IM = 0, IR = 1, IV = 4, IQ = 7, IW = 11, IY = 14;
 // compact df/dx slots of the stage buffer (see model_eval)
 constexpr int SA_A = 42;
-// the model has the RCS-torque controls (nu = 7)
+// the model has the RCS-torque controls (nu = 7) and reads the inertia J_B
 #define PDG_MODEL_NU_ALT 7
+#define PDG_MODEL_USES_INERTIA 1
 
 // ---------------------------------------------------------------------------
 // Sec. 5 model.  One call evaluates, at (x, u): f = s (F, sum |g|_+^2), the
