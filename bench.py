@@ -37,10 +37,10 @@ METRIC = "converged PDG SCP solves/s on 1 GB300, batch 16384, N=15; % FP64/FP32 
 # hash (profiles/ has the summaries); reported only while the sources match.
 PROFILED_TRAFFIC = {
     # ncu (dram__bytes_read.sum, dram__bytes_write.sum) of k_persistent<double,4,1>:
-    # 6-DoF on 456 instances (one per CTA slot), 12.11 MB read + 66.08 MB written;
-    # 3-DoF on 608 instances at its tuned 128 threads, 3.066 MB read + 0.064 MB written
-    "b0182b8a034afb4f": {("6dof", "fp64", 4, 15, "persistent"): 78.19e6 / 456,
-                         ("3dof", "fp64", 4, 15, "persistent"): 3.130e6 / 608},
+    # 6-DoF on 456 instances (one per CTA slot), 12.09 MB read + 66.87 MB written;
+    # 3-DoF on 608 instances at its tuned 128 threads, 3.261 MB read + 0.066 MB written
+    "2d39878f65c21628": {("6dof", "fp64", 4, 15, "persistent"): 78.96e6 / 456,
+                         ("3dof", "fp64", 4, 15, "persistent"): 3.326e6 / 608},
 }
 
 
