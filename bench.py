@@ -228,7 +228,7 @@ def run_grad(a):
     """Gradient workload: B dispersed instances, d(fuel, touchdown)/d(x0, m_wet)."""
     import torch
 
-    from paper_2404_18034_gb300 import build, inputs
+    from paper_2404_18034_gb300 import build, flops, inputs
     from paper_2404_18034_gb300.pdg_mc import Solver
     build.build()
     dev = torch.device("cuda", 0)
@@ -254,16 +254,75 @@ def run_grad(a):
             torch.cuda.synchronize(dev)
             ms.append(e0.elapsed_time(e1))
             ok += int((o["status"] <= 1).sum().item())
-    line = {"metric": "gradients d(fuel, touchdown)/d(x0, m_wet) per second on 1 GB300, batch 4096, N=15",
+    # algorithmic flops of one step from the counters of the same solve: the
+    # forward solve, plus the adjoint of its last SCP iteration counted as the
+    # PIPG loop twice (recomputed from checkpoints, then reversed), the
+    # first interval's discretization in dual arithmetic (3 flops per real
+    # flop) along the NX - 1 directions of x0, and the touchdown interval twice
+    sol = S.solve(x0, mode=1, trace=True)
+    torch.cuda.synchronize(dev)
+    scp = sol["scp_iters"].cpu().numpy()
+    tr = sol["trace"].cpu().numpy()
+    live = o["status"].cpu().numpy() <= 1
+    N, nu, nsub = a.nodes, p["nu"], p["rk4_substeps"]
+    fwd = flops.solve_flops(np.full(a.batch, N), nu, nsub, scp, tr[:, :, 0].sum(1), sol["pipg_iters"].cpu().numpy(),
+                            a.model)
+    last_pipg = tr[np.arange(a.batch), np.maximum(scp - 1, 0), 1]
+    one = flops.discretization(2, nu, nsub, a.model)
+    adj = float(np.sum(live * (2.0 * last_pipg * flops.pipg_iter(N, nu, a.model)
+                               + (3.0 * (S.nx - 1) + 2.0) * one)))
+    achieved = (fwd + adj) / (float(np.mean(ms)) * 1e-3) / 1e12
+    peak = SMS * FMA_PER_CLK["fp64"] * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    cpu = None if a.no_cpu else cpu_grad_baseline(p, a, x0.cpu().numpy())
+    line = {"metric": f"gradients d(fuel, touchdown)/d(x0, m_wet) per second on 1 GB300, batch {a.batch}, N={a.nodes}",
             "value": ok / (sum(ms) * 1e-3), "unit": "grads/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"pdg{a.model}_grad_{a.dispersion}_B{a.batch}_N{a.nodes}_fp64", "batch": a.batch,
-                       "nodes": a.nodes, "l2": "256 MiB buffer written between timed steps",
+                       "nodes": a.nodes, "model": a.model, "l2": "256 MiB buffer written between timed steps",
                        "includes": "the forward solve and the adjoint of its last SCP iteration"},
-            "clocks": clk.summary(), "gpu_launches": 2 * a.steps}
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_persistent + k_grad (one gradient step)",
+                         "flops_per_launch": fwd + adj, "flops_forward": fwd, "flops_adjoint": adj,
+                         "peak_source": f"derived: {SMS} SMs x 2 FP64 FMA/clk x 2 flop x {MAX_SM_MHZ:.0f} MHz"},
+            "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": 2 * a.steps}
     print(json.dumps(line), flush=True)
     S.close()
+
+
+def cpu_grad_baseline(p, a, x0h, budget_s: float = 12.0):
+    """The oracle's gradient as the tests take it -- a free solve, then
+    central differences (h = 1e-6) of its last SCP iteration along every
+    direction of x0 -- on the first instances of the batch, one thread per
+    host core (the oracle's ctypes calls release the GIL)."""
+    import concurrent.futures as cf
+
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+
+    def grad_one(x):
+        r = oracle.solve(p, a.nodes, x)
+        X, U, ws, sig, n = oracle.final_iteration_state(p, a.nodes, x, r["trace"], r["scp_iters"])
+        g = np.zeros((len(x), 2))
+        for j in range(len(x)):
+            e = np.zeros(len(x)); e[j] = 1e-6
+            g[j] = (np.array(oracle.final_iteration_outputs(p, x + e, X, U, ws, sig, n))
+                    - np.array(oracle.final_iteration_outputs(p, x - e, X, U, ws, sig, n))) / 2e-6
+        return r["status"] <= 1
+
+    t0 = time.perf_counter()
+    grad_one(x0h[0])
+    per = time.perf_counter() - t0
+    sample = int(min(a.batch, max(cores, round(budget_s * cores / max(per, 1e-6)))))
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(cores) as ex:
+        done = sum(ex.map(grad_one, list(x0h[:sample])))
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "grads/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} of the {a.batch} instances (FP64 oracle: free solve, then central differences "
+                      f"of its last SCP iteration along the {x0h.shape[1]} directions of x0; {cores} threads, "
+                      f"{dt:.1f} s)"}
 
 
 def fp32_error(p, a, S32, x0, Ns, out32, mode, dev):
