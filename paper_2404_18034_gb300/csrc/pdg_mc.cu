@@ -129,7 +129,7 @@ k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
     unsigned long long t_start;
     long long ptot;
     double defect, sigma;
-    int b, pit;
+    int b, pit, over;
   } C;
   // shape-class launch: this grid serves the instances perm[class_off[cls] ..
   // class_off[cls + 1]) (all of one node count)
@@ -164,7 +164,13 @@ k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
     __syncthreads();
     int stat = PDG_MAX_SCP, j;
     for (j = 1; j <= P.scp_jmax; ++j) {
-      if (P.budget_ns > 0.0 && double(globaltimer_ns() - C.t_start) > P.budget_ns) { stat = PDG_BUDGET; --j; break; }
+      if (P.budget_ns > 0.0) {
+        // one clock reading decides for the whole CTA: threads that read the
+        // clock on either side of the limit would part at the next barrier
+        if (threadIdx.x == 0) C.over = double(globaltimer_ns() - C.t_start) > P.budget_ns;
+        __syncthreads();
+        if (C.over) { stat = PDG_BUDGET; --j; break; }
+      }
       if (rec) {  // reference and warm start of this SCP iteration (the last one is kept)
         double* rc = rec + (size_t)C.b * rec_stride;
         const int n = L.N, ow = n * (NX + NU), nw = L.img - L.xh;
