@@ -88,7 +88,12 @@ __host__ __device__ inline AdjLay make_adj(const Lay& L, int nu, int threads) {
 // One PIPG_custom iteration on the state (xt .. vth) in shared memory, with no
 // stop test, recording the projection masks; with update = false the state is
 // left as it was (the intermediates x_hat, u_hat, mu, phi, theta, 2z - z~ are
-// written either way).
+// written either way).  Like the solve's PIPG step it is branch-free where a
+// branch would split a warp: on GB300 every FP64 warp instruction costs a slot
+// of the FP64 pipe whatever its active lanes.  Blocks that do not exist (the
+// last node's A, the first node's B^+, the last node's B^-) are read at a valid
+// index and their products discarded by a select; the CTCS terms of the y
+// component and the cost term of m_N ride on 0/1-weighted FMAs.
 template <int NU>
 __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, double* sm, double alpha,
                                double beta, double c1, double rho, bool update) {
@@ -106,22 +111,25 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
   double* vth = sm + L.vth;
   double* dx = sm + L.dx;
   double* du = sm + L.du;
-  const double wcost = P.w_cost, wep = P.w_ep;
+  const double acost = alpha * P.w_cost, wep = P.w_ep;
   for (int t = tid; t < PX + PU; t += T) {
     if (t < PX) {
       if (t < nxk) {
         const int k = t / NX + 1, i = t - NX * (k - 1), o = k * NX + i;
+        const bool last = k == N - 1;
+        const int km = last ? 0 : k;
         const double xv = xt[o];
-        double G = -vph[(k - 1) * NX + i];
-        if (k < N - 1) {
-          for (int r = 0; r < NX; ++r) G += Am[(k * NX + r) * NX + i] * vph[k * NX + r];
-          if (i == IY) G -= vth[k];
-        }
-        if (i == IY) G += vth[k - 1];
-        if (k == N - 1 && i == IM) G -= wcost;
-        double xn = c1 * xv - alpha * G;
-        if (k == N - 1 && P.fix_f[i]) xn = sm[L.zf + i];
-        dx[o] = 2.0 * xn - xv;
+        const double tdk = vth[k - 1] - (last ? 0.0 : vth[k]);
+        const double G0 = fma(i == IY ? 1.0 : 0.0, tdk, -vph[(k - 1) * NX + i]);
+        double Gc = G0;
+        const double* a = Am + km * NX * NX + i;
+        const double* f = vph + km * NX;
+        for (int r = 0; r < NX; ++r) Gc = fma(a[r * NX], f[r], Gc);
+        const double G = last ? G0 : Gc;
+        const double cost = (last && i == IM) ? acost : 0.0;
+        double xn = fma(-alpha, G, fma(c1, xv, cost));
+        xn = (last && P.fix_f[i]) ? sm[L.zf + i] : xn;
+        dx[o] = fma(2.0, xn, -xv);
         sm[L.xh + o] = xn;
         if (update) xt[o] = xv + rho * (xn - xv);
       }
@@ -129,27 +137,36 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
       const int q = t - PX;
       if (q < N * NU) {
         const int k = q / NU, cc = q - NU * k;
+        const bool hasM = k < N - 1, hasP = k > 0;
+        const int km = hasM ? k : 0, kp = hasP ? k - 1 : 0;
         const double uv = ut[q];
-        double G = 0;
-        if (k < N - 1)
-          for (int r = 0; r < NX; ++r) G += Bm[(k * NX + r) * NU + cc] * vph[k * NX + r];
-        if (k > 0)
-          for (int r = 0; r < NX; ++r) G += Bp[((k - 1) * NX + r) * NU + cc] * vph[(k - 1) * NX + r];
-        double un = c1 * uv - alpha * G;
-        double m = 0;
+        double Gm = 0;
+        {
+          const double* a = Bm + km * NX * NU + cc;
+          const double* f = vph + km * NX;
+          for (int r = 0; r < NX; ++r) Gm = fma(a[r * NU], f[r], Gm);
+        }
+        Gm = hasM ? Gm : 0.0;
+        double Gs = Gm;
+        {
+          const double* a = Bp + kp * NX * NU + cc;
+          const double* f = vph + kp * NX;
+          for (int r = 0; r < NX; ++r) Gs = fma(a[r * NU], f[r], Gs);
+        }
+        double un = fma(-alpha, hasP ? Gs : Gm, c1 * uv);
         if (cc == NU - 1) {
           const double lo = sm[L.lo + k], hi = sm[L.hi + k];
-          if (un <= lo) { un = lo; m = 1; }
-          else if (un >= hi) { un = hi; m = 1; }
-          sm[A.u_m + k] = m;
+          const bool clo = un <= lo, chi = !clo && un >= hi;
+          sm[A.u_m + k] = (clo || chi) ? 1.0 : 0.0;
+          un = clo ? lo : (chi ? hi : un);
         }
-        du[q] = 2.0 * un - uv;
+        du[q] = fma(2.0, un, -uv);
         sm[L.uh + q] = un;
         if (update) ut[q] = uv + rho * (un - uv);
       } else if (q < nuk) {
         const int i = q - N * NU;
         const double xv = xt[i], xn = sm[L.zi + i];
-        dx[i] = 2.0 * xn - xv;
+        dx[i] = fma(2.0, xn, -xv);
         sm[L.xh + i] = xn;
         if (update) xt[i] = xv + rho * (xn - xv);
       }
@@ -162,16 +179,17 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
         const int k = t / NX, i = t - NX * k;
         const double f = vph[t], a = nup[t], b = num[t];
         const double pa = a - alpha * (wep + f), pb = b - alpha * (wep - f);
-        const double mp = pa > 0 ? pa : 0.0, mm = pb > 0 ? pb : 0.0;
-        sm[A.mup_m + t] = pa > 0 ? 1.0 : 0.0;
-        sm[A.mum_m + t] = pb > 0 ? 1.0 : 0.0;
-        double r = sm[L.w + t] + ((2.0 * mp - a) - (2.0 * mm - b)) - dx[(k + 1) * NX + i];
-        for (int c = 0; c < NX; ++c) r += Am[(k * NX + i) * NX + c] * dx[k * NX + c];
+        const bool ma = pa > 0, mb = pb > 0;
+        const double mp = ma ? pa : 0.0, mm = mb ? pb : 0.0;
+        sm[A.mup_m + t] = ma ? 1.0 : 0.0;
+        sm[A.mum_m + t] = mb ? 1.0 : 0.0;
+        double r = sm[L.w + t] + (fma(2.0, mp, -a) - fma(2.0, mm, -b)) - dx[(k + 1) * NX + i];
+        for (int c = 0; c < NX; ++c) r = fma(Am[(k * NX + i) * NX + c], dx[k * NX + c], r);
         for (int c = 0; c < NU; ++c)
-          r += Bm[(k * NX + i) * NU + c] * du[k * NU + c] + Bp[(k * NX + i) * NU + c] * du[(k + 1) * NU + c];
+          r = fma(Bp[(k * NX + i) * NU + c], du[(k + 1) * NU + c], fma(Bm[(k * NX + i) * NU + c], du[k * NU + c], r));
         sm[L.mup + t] = mp;
         sm[L.mum + t] = mm;
-        sm[L.phi + t] = f + beta * r;
+        sm[L.phi + t] = fma(beta, r, f);
         if (update) {
           nup[t] = a + rho * (mp - a);
           num[t] = b + rho * (mm - b);
@@ -183,9 +201,10 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
       if (k < N - 1) {
         const double hy = dx[(k + 1) * NX + IY] - dx[k * NX + IY] - sm[L.eps + k];
         const double v = vth[k];
-        const double pt = v + beta * hy;
-        const double tn = pt > 0 ? pt : 0.0;
-        sm[A.th_m + k] = pt > 0 ? 1.0 : 0.0;
+        const double pt = fma(beta, hy, v);
+        const bool m = pt > 0;
+        const double tn = m ? pt : 0.0;
+        sm[A.th_m + k] = m ? 1.0 : 0.0;
         sm[L.th + k] = tn;
         if (update) vth[k] = v + rho * (tn - v);
       }
@@ -198,12 +217,16 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
 // state) goes from iteration j+1 to iteration j; the intermediates of
 // iteration j must be in place (grad_pipg_iter with update = false on S_j).
 // last: iteration j produced the output (x_hat, u_hat) whose cotangents are in
-// A.xob / A.uob.  Threads 0..NX-1 accumulate the cotangents of the first
-// interval's blocks hat A^-_1, hat B^-_1, hat B^+_1, hat w_1 in cA/cBm/cBp/cw.
+// A.xob / A.uob.  Threads 0..NX-1 (dual rows of the first interval) add the
+// cotangents of its blocks hat A^-_1, hat B^-_1, hat B^+_1, hat w_1 to their
+// rows of A.cA / A.cBm / A.cBp / A.cw in shared memory (no register carries
+// them through the reverse pass).
+// Branch-free like grad_pipg_iter: the recorded 0/1 projection masks weight
+// FMAs, and blocks that do not exist are read at a valid index and selected
+// away.
 template <int NU>
 __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& A, double* sm, double alpha,
-                                  double beta, double c1, double rho, bool last, double* accA, double* accBm,
-                                  double* accBp, double& accW) {
+                                  double beta, double c1, double rho, bool last) {
   const int N = L.N, T = blockDim.x, tid = threadIdx.x;
   const int nm = (N - 1) * NX, PM = round32(nm);
   const double* Am = sm + L.Am;
@@ -224,38 +247,35 @@ __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& 
   double* hb = sm + A.hb;
   double* Gb = sm + A.Gb;
   double* Gub = sm + A.Gub;
-  const double rhob = rho * beta;
+  const double rhob = rho * beta, omr = 1.0 - rho;
   // R1: dual rows and CTCS rows
   for (int t = tid; t < PM + 32; t += T) {
     if (t < PM) {
       if (t < nm) {
         const double r_ = rhob * vphb[t];
-        double fb = vphb[t];
-        const double mpb = rho * nupb[t] + 2.0 * r_;
-        const double mmb = rho * numb[t] - 2.0 * r_;
-        double ab = (1.0 - rho) * nupb[t] - r_;
-        double bb = (1.0 - rho) * numb[t] + r_;
-        if (sm[A.mup_m + t] > 0) { ab += mpb; fb -= alpha * mpb; }
-        if (sm[A.mum_m + t] > 0) { bb += mmb; fb += alpha * mmb; }
-        nupb[t] = ab;
-        numb[t] = bb;
-        vphb[t] = fb;
+        const double m1 = sm[A.mup_m + t], m2 = sm[A.mum_m + t];  // 0 or 1
+        const double mpb = fma(rho, nupb[t], 2.0 * r_);
+        const double mmb = fma(rho, numb[t], -2.0 * r_);
+        nupb[t] = fma(m1, mpb, fma(omr, nupb[t], -r_));
+        numb[t] = fma(m2, mmb, fma(omr, numb[t], r_));
+        vphb[t] = fma(alpha * m2, mmb, fma(-alpha * m1, mpb, vphb[t]));
         rb[t] = r_;
-        if (t < NX) {  // interval 1: cotangents of its blocks
-          for (int c = 0; c < NX; ++c) accA[c] += r_ * dx[c];
-          for (int c = 0; c < NU; ++c) { accBm[c] += r_ * du[c]; accBp[c] += r_ * du[NU + c]; }
-          accW += r_;
+        if (t < NX) {  // interval 1: cotangents of its blocks (row t)
+          for (int c = 0; c < NX; ++c) sm[A.cA + t * NX + c] = fma(r_, dx[c], sm[A.cA + t * NX + c]);
+          for (int c = 0; c < NU; ++c) {
+            sm[A.cBm + t * NU + c] = fma(r_, du[c], sm[A.cBm + t * NU + c]);
+            sm[A.cBp + t * NU + c] = fma(r_, du[NU + c], sm[A.cBp + t * NU + c]);
+          }
+          sm[A.cw + t] += r_;
         }
       }
     } else {
       const int k = t - PM;
       if (k < N - 1) {
+        const double m = sm[A.th_m + k];
         const double tb = rho * vthb[k];
-        double vb = (1.0 - rho) * vthb[k];
-        double h_ = 0;
-        if (sm[A.th_m + k] > 0) { vb += tb; h_ = beta * tb; }
-        vthb[k] = vb;
-        hb[k] = h_;
+        vthb[k] = fma(m, tb, omr * vthb[k]);
+        hb[k] = m * beta * tb;
       }
     }
   }
@@ -266,39 +286,39 @@ __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& 
     if (t < PX) {
       if (t < nx) {
         const int k = t / NX, i = t - NX * k;
-        double d = 0;
-        if (k < N - 1) {
-          for (int r = 0; r < NX; ++r) d += Am[(k * NX + r) * NX + i] * rb[k * NX + r];
-          if (i == IY) d -= hb[k];
-        }
-        if (k > 0) {
-          d -= rb[(k - 1) * NX + i];
-          if (i == IY) d += hb[k - 1];
-        }
-        double xhb = 2.0 * d + rho * xtb[t] + (last ? sm[A.xob + t] : 0.0);
-        double xb = -d + (1.0 - rho) * xtb[t];
-        double g = 0;
+        const bool hasA = k < N - 1, hasP = k > 0;
+        const int ka = hasA ? k : 0, kp = hasP ? k - 1 : 0;
+        double dA = 0;
+        const double* a = Am + ka * NX * NX + i;
+        const double* f = rb + ka * NX;
+        for (int r = 0; r < NX; ++r) dA = fma(a[r * NX], f[r], dA);
+        const double hd = (hasP ? hb[kp] : 0.0) - (hasA ? hb[ka] : 0.0);
+        double d = fma(i == IY ? 1.0 : 0.0, hd, hasA ? dA : 0.0);
+        d -= hasP ? rb[kp * NX + i] : 0.0;
+        const double xhb = fma(2.0, d, fma(rho, xtb[t], last ? sm[A.xob + t] : 0.0));
         const bool fixed = (k == 0) || (k == N - 1 && P.fix_f[i]);
-        if (!fixed) { xb += c1 * xhb; g = -alpha * xhb; }
-        xtb[t] = xb;
-        Gb[t] = g;
+        const double nf = fixed ? 0.0 : 1.0;
+        xtb[t] = fma(nf * c1, xhb, fma(omr, xtb[t], -d));
+        Gb[t] = (-alpha * nf) * xhb;
       }
     } else {
       const int q = t - PX;
       if (q < nuu) {
         const int k = q / NU, cc = q - NU * k;
-        double d = 0;
-        if (k < N - 1)
-          for (int r = 0; r < NX; ++r) d += Bm[(k * NX + r) * NU + cc] * rb[k * NX + r];
-        if (k > 0)
-          for (int r = 0; r < NX; ++r) d += Bp[((k - 1) * NX + r) * NU + cc] * rb[(k - 1) * NX + r];
-        double uhb = 2.0 * d + rho * utb[q] + (last ? sm[A.uob + q] : 0.0);
-        double ub = -d + (1.0 - rho) * utb[q];
-        double g = 0;
-        const bool clamped = (cc == NU - 1) && sm[A.u_m + k] > 0;
-        if (!clamped) { ub += c1 * uhb; g = -alpha * uhb; }
-        utb[q] = ub;
-        Gub[q] = g;
+        const bool hasM = k < N - 1, hasP = k > 0;
+        const int km = hasM ? k : 0, kp = hasP ? k - 1 : 0;
+        double dm = 0;
+        for (int r = 0; r < NX; ++r) dm = fma(Bm[(km * NX + r) * NU + cc], rb[km * NX + r], dm);
+        dm = hasM ? dm : 0.0;
+        double dp = dm;
+        for (int r = 0; r < NX; ++r) dp = fma(Bp[(kp * NX + r) * NU + cc], rb[kp * NX + r], dp);
+        const double d = hasP ? dp : dm;
+        const double uhb = fma(2.0, d, fma(rho, utb[q], last ? sm[A.uob + q] : 0.0));
+        // the mask is 0.0 or 1.0: test its bit pattern, not on the FP64 pipe
+        const bool clamped = (cc == NU - 1) && __double_as_longlong(sm[A.u_m + k]) != 0;
+        const double nc = clamped ? 0.0 : 1.0;
+        utb[q] = fma(nc * c1, uhb, fma(omr, utb[q], -d));
+        Gub[q] = (-alpha * nc) * uhb;
       }
     }
   }
@@ -308,26 +328,26 @@ __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& 
     if (t < PM) {
       if (t < nm) {
         const int k = t / NX, i = t - NX * k;
+        const int kk = k >= 1 ? k : 0;
         double fb = vphb[t];
-        if (k >= 1)
-          for (int c = 0; c < NX; ++c) fb += Am[(k * NX + i) * NX + c] * Gb[k * NX + c];
+        double fa = fb;
+        for (int c = 0; c < NX; ++c) fa = fma(Am[(kk * NX + i) * NX + c], Gb[kk * NX + c], fa);
+        fb = k >= 1 ? fa : fb;
         fb -= Gb[(k + 1) * NX + i];
         for (int c = 0; c < NU; ++c)
-          fb += Bm[(k * NX + i) * NU + c] * Gub[k * NU + c] + Bp[(k * NX + i) * NU + c] * Gub[(k + 1) * NU + c];
+          fb = fma(Bp[(k * NX + i) * NU + c], Gub[(k + 1) * NU + c], fma(Bm[(k * NX + i) * NU + c], Gub[k * NU + c], fb));
         vphb[t] = fb;
         if (t < NX) {
           const double ph = vph[t];
-          for (int c = 0; c < NU; ++c) { accBm[c] += ph * Gub[c]; accBp[c] += ph * Gub[NU + c]; }
+          for (int c = 0; c < NU; ++c) {
+            sm[A.cBm + t * NU + c] = fma(ph, Gub[c], sm[A.cBm + t * NU + c]);
+            sm[A.cBp + t * NU + c] = fma(ph, Gub[NU + c], sm[A.cBp + t * NU + c]);
+          }
         }
       }
     } else {
       const int k = t - PM;
-      if (k < N - 1) {
-        double vb = vthb[k];
-        if (k >= 1) vb -= Gb[k * NX + IY];
-        vb += Gb[(k + 1) * NX + IY];
-        vthb[k] = vb;
-      }
+      if (k < N - 1) vthb[k] = vthb[k] - (k >= 1 ? Gb[k * NX + IY] : 0.0) + Gb[(k + 1) * NX + IY];
     }
   }
   __syncthreads();

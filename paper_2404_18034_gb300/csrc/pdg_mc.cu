@@ -518,10 +518,10 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
     if (touch_out) touch_out[b] = e;
   }
   __syncthreads();
-  // reverse pass, segment by segment
-  double accA[NX], accBm[NU], accBp[NU], accW = 0.0;
-  for (int i = 0; i < NX; ++i) accA[i] = 0.0;
-  for (int i = 0; i < NU; ++i) { accBm[i] = 0.0; accBp[i] = 0.0; }
+  // reverse pass, segment by segment; the first interval's block cotangents
+  // accumulate in shared memory (cA, cBm, cBp, cw are contiguous)
+  for (int t = threadIdx.x; t < AL.gacc - AL.cA; t += blockDim.x) sm[AL.cA + t] = 0.0;
+  __syncthreads();
   for (int sgm = nck - 1; sgm >= 0; --sgm) {
     const int j0 = sgm * 50, j1 = min(n, j0 + 50);
     for (int t = threadIdx.x; t < ss; t += blockDim.x) state[t] = ckb[(size_t)sgm * ss + t];
@@ -535,18 +535,18 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
       for (int t = threadIdx.x; t < ss; t += blockDim.x) state[t] = seg[(size_t)(j - j0) * ss + t];
       __syncthreads();
       grad_pipg_iter<NU>(P, L, AL, sm, alpha, beta, c1, rho, false);
-      grad_pipg_reverse<NU>(P, L, AL, sm, alpha, beta, c1, rho, j == n - 1, accA, accBm, accBp, accW);
+      grad_pipg_reverse<NU>(P, L, AL, sm, alpha, beta, c1, rho, j == n - 1);
     }
   }
   // cotangents of the first interval's blocks, unscaled
   if (threadIdx.x < NX) {
     const int i = threadIdx.x;
-    for (int c = 0; c < NX; ++c) sm[AL.cA + i * NX + c] = accA[c] * P.Px[c] * P.Pxinv[i];
+    for (int c = 0; c < NX; ++c) sm[AL.cA + i * NX + c] *= P.Px[c] * P.Pxinv[i];
     for (int c = 0; c < NU; ++c) {
-      sm[AL.cBm + i * NU + c] = accBm[c] * P.Pu[c] * P.Pxinv[i];
-      sm[AL.cBp + i * NU + c] = accBp[c] * P.Pu[c] * P.Pxinv[i];
+      sm[AL.cBm + i * NU + c] *= P.Pu[c] * P.Pxinv[i];
+      sm[AL.cBp + i * NU + c] *= P.Pu[c] * P.Pxinv[i];
     }
-    sm[AL.cw + i] = accW * P.Pxinv[i];
+    sm[AL.cw + i] *= P.Pxinv[i];
   }
   __syncthreads();
   tangent_first_interval<NU>(P, L, AL, sm);
