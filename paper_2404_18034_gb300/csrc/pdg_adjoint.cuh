@@ -49,6 +49,7 @@ __device__ __forceinline__ Dual sqrt(Dual a) {
 // Scratch of the gradient kernel, appended after the solve layout.
 struct AdjLay {
   int ss;                       // size of the PIPG state (xt .. vth)
+  int sg;                       // size of one iteration's record for the reverse pass
   int Sb, rb, hb, Gb, Gub, mup_m, mum_m, th_m, u_m, Xo, Uo, xob, uob, cA, cBm, cBp, cw, gacc, td, tang, total;
 };
 
@@ -56,6 +57,8 @@ __host__ __device__ inline AdjLay make_adj(const Lay& L, int nu, int threads) {
   AdjLay A;
   const int N = L.N;
   A.ss = L.dx - L.xt;
+  // relaxed dual before the update, 2z - z~, the mu and theta masks, the box masks
+  A.sg = 3 * (N - 1) * NX + N * NX + N * nu + (N - 1) + N;
   int o = L.total;
   A.Sb = o; o += A.ss;
   A.rb = o; o += (N - 1) * NX;

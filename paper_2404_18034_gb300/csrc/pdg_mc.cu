@@ -522,19 +522,44 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
   // accumulate in shared memory (cA, cBm, cBp, cw are contiguous)
   for (int t = threadIdx.x; t < AL.gacc - AL.cA; t += blockDim.x) sm[AL.cA + t] = 0.0;
   __syncthreads();
+  // Within a segment the recomputation records, per iteration, what its
+  // reverse step reads (the relaxed dual before the update, 2z - z~ and the
+  // projection masks), so the reverse steps need no second recomputation.
+  const int nm = (N - 1) * NX, o1 = nm, o2 = o1 + N * NX, o3 = o2 + N * NU, o4 = o3 + nm, o5 = o4 + nm,
+            o6 = o5 + (N - 1);
   for (int sgm = nck - 1; sgm >= 0; --sgm) {
     const int j0 = sgm * 50, j1 = min(n, j0 + 50);
     for (int t = threadIdx.x; t < ss; t += blockDim.x) state[t] = ckb[(size_t)sgm * ss + t];
     __syncthreads();
     for (int j = j0; j < j1; ++j) {
-      for (int t = threadIdx.x; t < ss; t += blockDim.x) seg[(size_t)(j - j0) * ss + t] = state[t];
-      __syncthreads();
+      double* e = seg + (size_t)(j - j0) * AL.sg;
+      // the iteration's first write to vph comes after the barrier that ends its primal phase
+      for (int t = threadIdx.x; t < nm; t += blockDim.x) e[t] = sm[L.vph + t];
       grad_pipg_iter<NU>(P, L, AL, sm, alpha, beta, c1, rho, true);
+      for (int t = threadIdx.x; t < AL.sg - o1; t += blockDim.x) {
+        const int u = o1 + t;
+        e[u] = u < o2 ? sm[L.dx + (u - o1)]
+             : u < o3 ? sm[L.du + (u - o2)]
+             : u < o4 ? sm[AL.mup_m + (u - o3)]
+             : u < o5 ? sm[AL.mum_m + (u - o4)]
+             : u < o6 ? sm[AL.th_m + (u - o5)]
+                      : sm[AL.u_m + (u - o6)];
+      }
+      __syncthreads();  // the next iteration overwrites 2z - z~ and the masks
     }
     for (int j = j1 - 1; j >= j0; --j) {
-      for (int t = threadIdx.x; t < ss; t += blockDim.x) state[t] = seg[(size_t)(j - j0) * ss + t];
+      const double* e = seg + (size_t)(j - j0) * AL.sg;
+      for (int u = threadIdx.x; u < AL.sg; u += blockDim.x) {
+        const double v = e[u];
+        if (u < o1) sm[L.vph + u] = v;
+        else if (u < o2) sm[L.dx + (u - o1)] = v;
+        else if (u < o3) sm[L.du + (u - o2)] = v;
+        else if (u < o4) sm[AL.mup_m + (u - o3)] = v;
+        else if (u < o5) sm[AL.mum_m + (u - o4)] = v;
+        else if (u < o6) sm[AL.th_m + (u - o5)] = v;
+        else sm[AL.u_m + (u - o6)] = v;
+      }
       __syncthreads();
-      grad_pipg_iter<NU>(P, L, AL, sm, alpha, beta, c1, rho, false);
       grad_pipg_reverse<NU>(P, L, AL, sm, alpha, beta, c1, rho, j == n - 1);
     }
   }
@@ -1136,7 +1161,8 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
   const int rec_stride = h->n_max * (NX + NU) + (Lg.img - Lg.xh) + 2;
   const int ss = Ag.ss;
   const int nck_max = (h->p.pipg_jmax + 49) / 50;
-  const long long ck_stride = (long long)(nck_max + 50) * ss;
+  // checkpoints of the state every 50 iterations, then one segment's records
+  const long long ck_stride = (long long)nck_max * ss + 50LL * Ag.sg;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bX = sizeof(double) * (size_t)B * h->n_max * NX, bU = sizeof(double) * (size_t)B * h->n_max * NU;
   const size_t bB = sizeof(double) * B, bI = sizeof(int) * B, bL = sizeof(long long) * B;
