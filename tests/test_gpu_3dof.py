@@ -219,3 +219,31 @@ def test_edge_cases_and_host_api(torch_cuda, inputs):
         np.testing.assert_array_equal(dev[k].cpu().numpy(), host[k])
     S.close()
 
+
+def test_full_size_sampled(torch_cuda, oracle, inputs):
+    """The 3-DoF benchmark workload (B = 16384, N = 15, FP64, persistent at the
+    tuned launch shape): sampled instances by oracle replay, invariants on all."""
+    torch = torch_cuda
+    from paper_2404_18034_gb300.autotune import DEFAULT_CACHE
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    p = inputs.load_params(model="3dof")
+    S = Solver(p, 15, 0, tune_cache=DEFAULT_CACHE, mode=1)
+    B = 16384
+    x0 = inputs.dispersion(p, B, inputs.config_seed(2), "bj")
+    out = S.solve(_d(torch, x0), mode=1, trace=True)
+    torch.cuda.synchronize()
+    o = {k: v.cpu().numpy() for k, v in out.items()}
+    hist = np.bincount(o["status"], minlength=5)
+    assert hist[3:].sum() == 0 and hist[0] > 0.99 * B, hist
+    ok = o["status"] != 2
+    np.testing.assert_allclose(o["X"][ok, 0, :7], x0[ok], atol=1e-12)
+    assert np.all(o["trace"][:, :, 1].sum(1) == o["pipg_iters"])
+    rng = np.random.default_rng(1)
+    conv = np.nonzero(o["status"] == 0)[0]
+    for b in list(rng.choice(conv, 8, replace=False)) + [conv[0], conv[-1]]:
+        r = replay_instance(oracle, p, x0[b], 15, o["trace"][b], int(o["scp_iters"][b]))
+        assert o["status"][b] == r["status"], (b, o["status"][b], r["status"])
+        assert_scaled_close(o["X"][b], r["X"], p["P_x"], what=f"X b{b}")
+        assert abs(o["fuel"][b] - r["fuel"]) <= RTOL * max(abs(r["fuel"]), 0.5)
+    S.close()
+
