@@ -47,10 +47,11 @@ using namespace pdg;
 
 namespace {
 
-template <typename R, int NU, int PV>
-__device__ __forceinline__ int run_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force) {
+template <typename R, int NU, int PV, bool CK = false>
+__device__ __forceinline__ int run_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force,
+                                        double* ck = nullptr) {
   if constexpr (PV == 2) return phase_pipg_reg<R, NU>(P, L, sm, sigma, force);
-  else return phase_pipg<R, NU>(P, L, sm, sigma, force);
+  else return phase_pipg<R, NU, CK>(P, L, sm, sigma, force, ck);
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -113,7 +114,12 @@ __device__ void write_outputs(const Lay& L, const R* sm, int b, int Nmax, int st
 // ---------------------------------------------------------------------------
 // persistent form
 // ---------------------------------------------------------------------------
-template <typename R, int NU, int PV>
+// CK: the gradient solve's instantiation (FP64, PIPG form 1, rec set): each
+// SCP iteration also records the PIPG state every 50 iterations and the
+// final x_hat, u_hat in the instance's record, so that the adjoint does not
+// rerun the last PIPG loop forward.  Record of an instance (offsets for its N):
+// X_bar, U_bar | warm start | sigma, PIPG count | x_hat, u_hat | checkpoints.
+template <typename R, int NU, int PV, bool CK = false>
 __global__ void PDG_LB(R, PV)
 k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
              double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
@@ -189,7 +195,16 @@ k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
         int pit;
         const R sigma = phase_power<R, NU>(P, L, sm, 0, &pit);
         if (threadIdx.x == 0) { C.sigma = double(sigma); C.pit = pit; }
-        jit = run_pipg<R, NU, PV>(P, L, sm, sigma, 0);
+        if constexpr (CK) {
+          const int ow = L.N * (NX + NU), nw = L.img - L.xh;
+          double* ckp = rec + (size_t)C.b * rec_stride + ow + nw + 2 + ow;
+          jit = run_pipg<R, NU, PV, true>(P, L, sm, sigma, 0, ckp);
+          double* rf = rec + (size_t)C.b * rec_stride + ow + nw + 2;
+          for (int t = threadIdx.x; t < ow; t += blockDim.x)
+            rf[t] = double(t < L.N * NX ? sm[L.xh + t] : sm[L.uh + t - L.N * NX]);
+        } else {
+          jit = run_pipg<R, NU, PV>(P, L, sm, sigma, 0);
+        }
       }
       const int bb = C.b;
       if (rec && threadIdx.x == 0) {
@@ -443,7 +458,7 @@ __global__ void __launch_bounds__(256, 1)
 k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
        const double* __restrict__ rec, int rec_stride, const int* __restrict__ status,
        const double* __restrict__ gf_in, const double* __restrict__ gt_in, double* ck, long long ck_stride,
-       int nck_max, double* grad, double* fuel_out, double* touch_out) {
+       int nck_max, int ckrec, double* grad, double* fuel_out, double* touch_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double* sm = reinterpret_cast<double*>(smraw);
   const int b = blockIdx.x;
@@ -492,15 +507,23 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
   const double c1 = 1.0 - alpha * wp;
   const double rho = P.rho;
   double* ckb = ck + (size_t)b * ck_stride;
-  double* seg = ckb + (size_t)nck_max * ss;
+  double* seg = ckb + (ckrec ? (size_t)0 : (size_t)nck_max * ss);
   const int nck = (n + 49) / 50;
-  // forward pass of the final PIPG loop with a checkpoint every 50 iterations
-  for (int j = 0; j < n; ++j) {
-    if (j % 50 == 0) {
-      for (int t = threadIdx.x; t < ss; t += blockDim.x) ckb[(size_t)(j / 50) * ss + t] = state[t];
-      __syncthreads();
+  const double* cks = ckrec ? rc + (ow + nw + 2 + ow) : ckb;  // the checkpoints
+  if (ckrec) {
+    // the solve recorded the last PIPG loop's final iterate and checkpoints
+    for (int t = threadIdx.x; t < N * NX; t += blockDim.x) sm[L.xh + t] = rc[ow + nw + 2 + t];
+    for (int t = threadIdx.x; t < N * NU; t += blockDim.x) sm[L.uh + t] = rc[ow + nw + 2 + N * NX + t];
+    __syncthreads();
+  } else {
+    // forward pass of the final PIPG loop with a checkpoint every 50 iterations
+    for (int j = 0; j < n; ++j) {
+      if (j % 50 == 0) {
+        for (int t = threadIdx.x; t < ss; t += blockDim.x) ckb[(size_t)(j / 50) * ss + t] = state[t];
+        __syncthreads();
+      }
+      grad_pipg_iter<NU>(P, L, AL, sm, alpha, beta, c1, rho, true);
     }
-    grad_pipg_iter<NU>(P, L, AL, sm, alpha, beta, c1, rho, true);
   }
   // updated trajectory and the output functionals
   for (int t = threadIdx.x; t < N * NX; t += blockDim.x) sm[AL.Xo + t] = sm[L.Xb + t] + P.Px[t % NX] * sm[L.xh + t];
@@ -529,7 +552,7 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
             o6 = o5 + (N - 1);
   for (int sgm = nck - 1; sgm >= 0; --sgm) {
     const int j0 = sgm * 50, j1 = min(n, j0 + 50);
-    for (int t = threadIdx.x; t < ss; t += blockDim.x) state[t] = ckb[(size_t)sgm * ss + t];
+    for (int t = threadIdx.x; t < ss; t += blockDim.x) state[t] = cks[(size_t)sgm * ss + t];
     __syncthreads();
     for (int j = j0; j < j1; ++j) {
       double* e = seg + (size_t)(j - j0) * AL.sg;
@@ -658,6 +681,7 @@ struct pdg_handle {
   cudaEvent_t cls_events[NMAX + 1] = {};
   double* rec_ptr = nullptr;   // set only while a gradient solve runs
   int rec_stride = 0;
+  bool ck_rec = false;         // ... and whose record also holds the PIPG checkpoints
   void* gws = nullptr;
   size_t gws_bytes = 0;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -826,7 +850,12 @@ using PersistentFn = void (*)(const DParams, int, int, const double*, const int*
 template <typename R, int NU>
 using PlainPipgFn = void (*)(const DParams, int, int, const int*, PlainWs, const int*);
 template <typename R, int NU>
-static PersistentFn<R, NU> persistent_fn(int pv) { return pv == 2 ? k_persistent<R, NU, 2> : k_persistent<R, NU, 1>; }
+static PersistentFn<R, NU> persistent_fn(int pv, bool ck = false) {
+  if constexpr (sizeof(R) == 8) {
+    if (ck && pv == 1) return k_persistent<R, NU, 1, true>;
+  }
+  return pv == 2 ? k_persistent<R, NU, 2> : k_persistent<R, NU, 1>;
+}
 template <typename R, int NU>
 static PlainPipgFn<R, NU> plain_pipg_fn(int pv) { return pv == 2 ? k_plain_pipg<R, NU, 2> : k_plain_pipg<R, NU, 1>; }
 
@@ -839,6 +868,9 @@ struct Kern {
                          (const void*)k_plain_pipg<R, NU, 2>, (const void*)k_plain_update<R, NU>,
                          (const void*)k_subproblem<R, NU>};
     for (const void* f : fns) PDG_CUDA(h, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if constexpr (sizeof(R) == 8)
+      PDG_CUDA(h, cudaFuncSetAttribute(k_persistent<R, NU, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
     return 0;
   }
 };
@@ -855,7 +887,7 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
   if (L.ipw < 1 || make_lay(h->n_max, NU, pl.Tr).ipw < 1)
     return fail(h, PDG_EINVAL, "threads per CTA too small for one discretization interval");
   if (int rc = Kern<R, NU>::prepare(h, T, smem)) return rc;
-  const PersistentFn<R, NU> kp = persistent_fn<R, NU>(pl.pv);
+  const PersistentFn<R, NU> kp = persistent_fn<R, NU>(pl.pv, h->ck_rec && mode == 1);
   int occ = 0;
   PDG_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kp, T, smem));
   if (occ < 1) return fail(h, PDG_EINVAL, "solve kernel does not fit on an SM with this configuration");
@@ -1158,11 +1190,19 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
   const size_t smem_g = (size_t)Ag.total * sizeof(double);
   if (smem_g > 232448) return fail(h, PDG_EINVAL, "gradient kernel does not fit in shared memory for this n_max");
   if (h->p.rk4_substeps > 32) return fail(h, PDG_EINVAL, "gradients support at most 32 RK4 substeps");
-  const int rec_stride = h->n_max * (NX + NU) + (Lg.img - Lg.xh) + 2;
   const int ss = Ag.ss;
   const int nck_max = (h->p.pipg_jmax + 49) / 50;
-  // checkpoints of the state every 50 iterations, then one segment's records
-  const long long ck_stride = (long long)nck_max * ss + 50LL * Ag.sg;
+  // With the shared-memory PIPG form the solve itself records the last PIPG
+  // loop's checkpoints and final iterate (k_persistent's CK instantiation);
+  // otherwise k_grad reruns that loop forward and writes the checkpoints.
+  Plan pl;
+  std::string why;
+  if (!plan_for(h, h->n_max, &pl, &why)) return fail(h, PDG_EINVAL, why);
+  const bool ckrec = pl.pv == 1;
+  const int rec_stride = h->n_max * (NX + NU) + (Lg.img - Lg.xh) + 2 +
+                         (ckrec ? h->n_max * (NX + NU) + nck_max * ss : 0);
+  // per instance: [checkpoints of the state every 50 iterations,] one segment's records
+  const long long ck_stride = (ckrec ? 0LL : (long long)nck_max * ss) + 50LL * Ag.sg;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bX = sizeof(double) * (size_t)B * h->n_max * NX, bU = sizeof(double) * (size_t)B * h->n_max * NU;
   const size_t bB = sizeof(double) * B, bI = sizeof(int) * B, bL = sizeof(long long) * B;
@@ -1187,13 +1227,15 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
   double* ck = (double*)c;
   h->rec_ptr = rec;
   h->rec_stride = rec_stride;
+  h->ck_rec = ckrec;
   int rc = run_solve<double, NU>(h, B, x0, Ns, 1, X, U, tf, fu, st, sc, pi, nullptr, s);
   h->rec_ptr = nullptr;
   h->rec_stride = 0;
+  h->ck_rec = false;
   if (rc) return rc;
   PDG_CUDA(h, cudaFuncSetAttribute(k_grad<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g));
   k_grad<NU><<<B, Tg, smem_g, s>>>(h->dp, B, h->n_max, x0, Ns, rec, rec_stride, st, gf, gt, ck, ck_stride, nck_max,
-                                   grad, fuel_out, touch_out);
+                                   ckrec ? 1 : 0, grad, fuel_out, touch_out);
   PDG_CUDA(h, cudaGetLastError());
   if (status_out) PDG_CUDA(h, cudaMemcpyAsync(status_out, st, sizeof(int) * B, cudaMemcpyDeviceToDevice, s));
   return 0;

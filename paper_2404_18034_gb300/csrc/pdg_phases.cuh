@@ -324,8 +324,11 @@ template <bool B> struct ChkTag { static constexpr bool value = B; };
 
 // Returns the iterations run.  Extrapolations 2 z - z~ are written as fma:
 // the compiler would otherwise form z + z and subtract (two FP64 adds).
-template <typename R, int NU>
-__device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force) {
+// CK (gradient solves only): before iterations 1, 51, 101, ... the state
+// (x~, u~, nu~+-, phi~, theta~; nu~ unshifted) is copied to ck, one record of
+// L.dx - L.xt values per 50 iterations, for the adjoint's recomputation.
+template <typename R, int NU, bool CK = false>
+__device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force, double* ck = nullptr) {
   using OB = OrdBits<R>;
   using U = typename OB::U;
   const int N = L.N, T = blockDim.x, tid = threadIdx.x;
@@ -568,6 +571,17 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
   };
   int j;
   for (j = 1; j <= jmax; ++j) {
+    if constexpr (CK) {
+      if (((j - 1) % 50) == 0) {
+        const int ss = L.dx - L.xt, o0 = L.nup - L.xt, o1 = L.vph - L.xt;
+        double* c = ck + (size_t)((j - 1) / 50) * ss;
+        for (int t = tid; t < ss; t += T) {
+          const double v = double(sm[L.xt + t]);
+          c[t] = (t >= o0 && t < o1) ? v + double(aw) : v;
+        }
+        __syncthreads();  // the iteration overwrites the state
+      }
+    }
     if (force <= 0 && jcheck > 0 && (j % jcheck) == 0) {
       if (iterate(ChkTag<true>{})) break;
     } else {

@@ -31,15 +31,22 @@ def _fd(oracle, p, x0, X, U, ws, sig, n, h=1e-6):
 @pytest.mark.parametrize("nu,N,B,ov", [(4, 15, 6, {}), (4, 10, 3, {}), (7, 12, 2, {}),
                                         (4, 12, 3, {"glide_slope": 1, "dt_min": 0.3, "dt_max": 0.55}),
                                         (4, 15, 4, {"model": "3dof"}),
-                                        (4, 11, 3, {"model": "3dof", "glide_slope": 1})])
+                                        (4, 11, 3, {"model": "3dof", "glide_slope": 1}),
+                                        (4, 10, 3, {"pipg_form": 2})])
 def test_gradient_matches_oracle_finite_differences(torch_cuda, oracle, inputs, nu, N, B, ov):
     """Both models: the 6-DoF one of Sec. 5 and the 3-DoF instance of the
-    template (gradient d L / d (m_wet, r, v) there)."""
+    template (gradient d L / d (m_wet, r, v) there).  With the shared-memory
+    PIPG form the solve records the last PIPG loop's checkpoints for the
+    adjoint; with the register form (pipg_form 2) the adjoint reruns that
+    loop itself: both paths are checked."""
     torch = torch_cuda
     from paper_2404_18034_gb300.pdg_mc import Solver
     ov = dict(ov)
+    form = ov.pop("pipg_form", 0)
     p = inputs.load_params(nu=nu, model=ov.pop("model", None), **ov)
     S = Solver(p, N)
+    if form:
+        S.set_pipg_form(form)
     x0 = inputs.dispersion(p, B, inputs.config_seed(3), "bj")
     d = torch.from_numpy(x0).cuda()
     sol = S.solve(d, mode=1, trace=True)
