@@ -37,10 +37,10 @@ METRIC = "converged PDG SCP solves/s on 1 GB300, batch 16384, N=15; % FP64/FP32 
 # hash (profiles/ has the summaries); reported only while the sources match.
 PROFILED_TRAFFIC = {
     # ncu (dram__bytes_read.sum, dram__bytes_write.sum) of k_persistent<double,4,1>:
-    # 6-DoF on 456 instances (one per CTA slot), 12.04 MB read + 66.14 MB written;
-    # 3-DoF on 608 instances at its tuned 128 threads, 3.037 MB read + 0.065 MB written
-    "387ca00fe8ebb2d5": {("6dof", "fp64", 4, 15, "persistent"): 78.19e6 / 456,
-                         ("3dof", "fp64", 4, 15, "persistent"): 3.102e6 / 608},
+    # 6-DoF on 456 instances (one per CTA slot), 11.98 MB read + 67.33 MB written;
+    # 3-DoF on 608 instances at its tuned 128 threads, 3.131 MB read + 0.073 MB written
+    "cdd8cf796075fbe7": {("6dof", "fp64", 4, 15, "persistent"): 79.31e6 / 456,
+                         ("3dof", "fp64", 4, 15, "persistent"): 3.204e6 / 608},
 }
 
 
