@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--mode", default="persistent", choices=["persistent", "plain", "classed"])
-    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--batch", type=int, default=None, help="instances (default 16384; 4096 with --grad)")
     ap.add_argument("--nodes", type=int, default=15)
     ap.add_argument("--dispersion", default="bj", choices=["bj", "paper256", "nominal"])
     ap.add_argument("--nu", type=int, default=4, choices=[4, 7], help="7: the paper's model with the RCS torque")
@@ -516,6 +516,8 @@ def run_ours(a):
 
 def main():
     a = parse()
+    if a.batch is None:
+        a.batch = 4096 if a.grad else 16384
     if a.impl == "reference":
         run_reference(a)
     elif a.grad:
