@@ -191,7 +191,11 @@ int pdg_mc_scp_step(pdg_handle* h, int B, const double* x0, const int* n_nodes,
  *                            touchdown = 0.5 sum_{E_f} ((x_prop,N - z_f)/P_x)^2,
  *                            x_prop,N the RK4 propagation of the last interval
  *   status [B]               solve status (NULL = not written); instances that
- *                            end non-finite or with bad input get zero gradient */
+ *                            end non-finite or with bad input get zero gradient
+ * The handle's gradient workspace (grown on demand, kept until destroy) holds,
+ * per instance, the last SCP iteration's record with its PIPG checkpoints and
+ * one 50-iteration segment of the adjoint's records: about 0.7 MB at
+ * n_max = 15 and pipg_jmax = 2000 (2.8 GB for 4096 instances). */
 int pdg_mc_grad_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes,
                       const double* dL_dfuel, const double* dL_dtouch, double* grad_x0,
                       double* fuel, double* touch, int* status, void* cuda_stream);
