@@ -522,3 +522,18 @@ def test_glide_slope_and_time_bounds_match_oracle(torch_cuda, oracle, inputs, fo
         s = o["U"][b, :, -1]
         dt = (s[:-1] + s[1:]) / (2 * (n_max - 1))
         assert dt.min() >= 0.3 - 1e-9 and dt.max() <= 0.5 + 1e-9 and o["tf"][b] <= 6.6 + 1e-9
+
+
+@pytest.mark.parametrize("model", ["6dof", "3dof"])
+def test_maximum_node_count_matches_oracle_replay(torch_cuda, oracle, inputs, model):
+    """N = 32, the largest node count the kernels are built for (the 6-DoF
+    image then takes one CTA per SM), whole solves against the replay."""
+    torch = torch_cuda
+    from paper_2404_18034_gb300.pdg_mc import Solver
+    p = inputs.load_params(model=model)
+    S = Solver(p, 32)
+    x0 = inputs.dispersion(p, 4, 77, "bj")
+    o = _solve_and_replay(torch, oracle, inputs, p, S, x0, np.full(4, 32, np.int32), 1, range(4), converged_only=True)
+    assert np.all(o["status"] <= 1)
+    S.close()
+
