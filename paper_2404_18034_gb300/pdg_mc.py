@@ -183,6 +183,8 @@ class Solver:
         """library: path of a library built from a model header of the
         caller's (build.build_model); params["model"] is then "custom"."""
         self.model = model_of(params)
+        if self.model == "custom" and library is None:
+            raise ValueError('params["model"] == "custom" needs library= (a library from build.build_model)')
         self.lib = load_library(library, model=self.model)
         self.nx = int(self.lib.pdg_mc_model_nx())
         self.params = params
