@@ -1,7 +1,8 @@
-// pdg_device.cuh -- device side of the batched solver: parameters, per-instance
-// shared-memory layout, the 6-DoF model with its compact Jacobians, and the
-// phases of one SCP iteration (arXiv 2404.18034, Sec. 2-5).  One CTA owns one
-// instance at a time; every block of its subproblem lives in shared memory.
+// pdg_device.cuh -- device side of the batched solver: parameters, the
+// per-instance shared-memory layout, the choice of the model (the 6-DoF model
+// of Sec. 5, the 3-DoF model, or a caller's header) and block reductions
+// (arXiv 2404.18034, Sec. 2-5).  One CTA owns one instance at a time; every
+// block of its subproblem lives in shared memory.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -25,7 +25,7 @@ __device__ void phase_init_guess(const DParams& P, const Lay& L, R* sm) {
 // the prescaled blocks hat A^-_k, hat B^-_k, hat B^+_k, hat w_k.  Thread
 // mapping: lane l of warp 0 integrates x on interval k0 + l and evaluates the
 // compact Jacobians at each RK4 stage (its RK4 state lives in the interval's
-// stage buffer); every thread of warps 1.. holds one STM column (15 + 2 NU per
+// stage buffer); every thread of warps 1.. holds one STM column (NX + 2 NU per
 // interval) in registers.  Intervals are processed in waves of L.ipw.
 // Returns max_k |hat w_k|_inf (the scaled defect) on every thread.
 #ifdef PDG_DISC_INLINE
@@ -315,8 +315,8 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
 // extrapolated dual of the dynamics rows; the stop test compares iterates j+1
 // and j (the warm start being iterate 0).
 // Work split, every task range padded to whole warps:
-//   primal phase: x_hat of nodes 2..N (15 (N-1) tasks), then u_hat (G lanes
-//     per node) and the fixed node 1 (15 tasks);
+//   primal phase: x_hat of nodes 2..N (NX (N-1) tasks), then u_hat (G lanes
+//     per node) and the fixed node 1 (NX tasks);
 //   dual phase: row i of interval k updates mu^+-, nu^+- (they read the same
 //     extrapolated dual entry) and then phi; then the CTCS rows theta_k, whose
 //     warp also forms the per-node differences td for the next primal step.
