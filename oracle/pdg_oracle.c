@@ -662,6 +662,15 @@ static double maxd(double a, double b) { return a > b ? a : b; }
 /* ------------------------------------------------------------------------ */
 
 double orc_power(const orc_params* p, const orc_qp* qp, const orc_pd* start, int force_iters, int* iters) {
+  return orc_power_m(p, qp, start, force_iters, iters, NULL);
+}
+
+/* Relative margin (a - b) / b of a test a <= b with b > 0: the test passes
+ * exactly when the margin is <= 0. */
+static double margin(double a, double b) { return (a - b) / b; }
+
+double orc_power_m(const orc_params* p, const orc_qp* qp, const orc_pd* start, int force_iters, int* iters,
+                   double* margins) {
   const int N = qp->N, nu = qp->nu;
   orc_pd z;
   orc_pd_alloc(&z, N, nu);
@@ -714,6 +723,7 @@ double orc_power(const orc_params* p, const orc_qp* qp, const orc_pd* start, int
       ss += sqn(NX, z.xh + k * NX) + sqn(nu, z.uh + k * nu) + sqn(NX, z.mup + k * NX) + sqn(NX, z.mum + k * NX);
     ss += sqn(NX, z.xh + (N - 1) * NX) + sqn(nu, z.uh + (N - 1) * nu);
     sstar = sqrt(ss);
+    if (margins) margins[j - 1] = margin(fabs(sstar - sig), p->pow_eps_abs + p->pow_eps_rel * maxd(sstar, sig));
     if (force_iters <= 0 && fabs(sstar - sig) <= p->pow_eps_abs + p->pow_eps_rel * maxd(sstar, sig)) break;
     if (j < jmax) sig = sstar;
   }
@@ -739,6 +749,27 @@ static int stop_custom(const orc_params* p, const orc_qp* qp, const orc_pd* a, c
   double rd = maxd(infd(nm, a->phi, b->phi), infd(N - 1, a->th, b->th));
   return zd <= p->pipg_eps_abs + p->pipg_eps_rel * maxd(za, zb) &&
          rd <= p->pipg_eps_abs + p->pipg_eps_rel * maxd(ra, rb);
+}
+
+/* The same test as a relative margin: the larger of the primal and the dual
+ * margins, <= 0 exactly when stop_custom terminates. */
+static double stop_margin(const orc_params* p, const orc_qp* qp, const orc_pd* a, const orc_pd* b) {
+  const int N = qp->N, nu = qp->nu;
+  int nx = N * NX, nuu = N * nu, nm = (N - 1) * NX;
+  double za = maxd(maxd(infn(nx, a->xh), infn(nuu, a->uh)), maxd(infn(nm, a->mup), infn(nm, a->mum)));
+  double zb = maxd(maxd(infn(nx, b->xh), infn(nuu, b->uh)), maxd(infn(nm, b->mup), infn(nm, b->mum)));
+  double zd = maxd(maxd(infd(nx, a->xh, b->xh), infd(nuu, a->uh, b->uh)),
+                   maxd(infd(nm, a->mup, b->mup), infd(nm, a->mum, b->mum)));
+  double ra = maxd(infn(nm, a->phi), infn(N - 1, a->th));
+  double rb = maxd(infn(nm, b->phi), infn(N - 1, b->th));
+  double rd = maxd(infd(nm, a->phi, b->phi), infd(N - 1, a->th, b->th));
+  return maxd(margin(zd, p->pipg_eps_abs + p->pipg_eps_rel * maxd(za, zb)),
+              margin(rd, p->pipg_eps_abs + p->pipg_eps_rel * maxd(ra, rb)));
+}
+
+int orc_stop_custom(const orc_params* p, const orc_qp* qp, const orc_pd* a, const orc_pd* b, double* m) {
+  if (m) *m = stop_margin(p, qp, a, b);
+  return stop_custom(p, qp, a, b);
 }
 
 static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -775,6 +806,11 @@ static void soc_project_uhat(const orc_qp* qp, int k, double* uh) {
 }
 
 int orc_pipgc(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, int force_iters) {
+  return orc_pipgc_m(p, qp, sigma, ws, force_iters, NULL);
+}
+
+int orc_pipgc_m(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, int force_iters,
+                double* margins) {
   const int N = qp->N, nu = qp->nu;
   const double wp = qp->w_prox;
   orc_pd cur, prev, til;
@@ -877,6 +913,8 @@ int orc_pipgc(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, i
       vph[i] = (1.0 - rho) * vph[i] + rho * cur.phi[i];
     }
     for (int k = 0; k < N - 1; k++) vth[k] = (1.0 - rho) * vth[k] + rho * cur.th[k];
+    if (margins && p->pipg_jcheck > 0 && j % p->pipg_jcheck == 0)
+      margins[j / p->pipg_jcheck - 1] = stop_margin(p, qp, &cur, &prev);
     if (force_iters <= 0 && p->pipg_jcheck > 0 && j % p->pipg_jcheck == 0) {
       if (stop_custom(p, qp, &cur, &prev)) break;
     }
@@ -1119,6 +1157,14 @@ void orc_init_guess(const orc_params* p, int N, const double* x0, double* X, dou
 int orc_scp_iterate(const orc_params* p, int N, const double* x0, double* X, double* U,
                     orc_pd* ws, int force_pow, int force_pipg, double force_sigma,
                     double* sigma, int* pow_it, int* pipg_it, double* defect, double* step) {
+  return orc_scp_iterate_m(p, N, x0, X, U, ws, force_pow, force_pipg, force_sigma, sigma, pow_it, pipg_it,
+                           defect, step, NULL, NULL);
+}
+
+int orc_scp_iterate_m(const orc_params* p, int N, const double* x0, double* X, double* U,
+                      orc_pd* ws, int force_pow, int force_pipg, double force_sigma,
+                      double* sigma, int* pow_it, int* pipg_it, double* defect, double* step,
+                      double* pow_margins, double* pipg_margins) {
   const int nu = p->nu;
   double* A = malloc(sizeof(double) * (N - 1) * NX * NX);
   double* Bm = malloc(sizeof(double) * (N - 1) * NX * nu);
@@ -1129,8 +1175,8 @@ int orc_scp_iterate(const orc_params* p, int N, const double* x0, double* X, dou
   orc_discretize(p, N, X, U, A, Bm, Bp, xp);
   orc_scale(p, N, x0, X, U, A, Bm, Bp, xp, &qp);
   int pit = 0;
-  double sg = force_sigma > 0 ? force_sigma : orc_power(p, &qp, ws, force_pow, &pit);
-  int jit = orc_pipgc(p, &qp, sg, ws, force_pipg);
+  double sg = force_sigma > 0 ? force_sigma : orc_power_m(p, &qp, ws, force_pow, &pit, pow_margins);
+  int jit = orc_pipgc_m(p, &qp, sg, ws, force_pipg, pipg_margins);
   double dfc = infn((N - 1) * NX, qp.w);
   double stp = maxd(infn(N * NX, ws->xh), infn(N * nu, ws->uh));
   for (int k = 0; k < N; k++) {
@@ -1173,6 +1219,12 @@ static int all_finite(int n, const double* a) {
  * budget y_N - y_1 <= (N-1) eps all within tolerance. */
 int orc_solve(const orc_params* p, int N, const double* x0, double* X, double* U,
               orc_result* res, int* trace, int replay, int replay_scp) {
+  return orc_solve_m(p, N, x0, X, U, res, trace, replay, replay_scp, NULL, NULL, NULL);
+}
+
+int orc_solve_m(const orc_params* p, int N, const double* x0, double* X, double* U,
+                orc_result* res, int* trace, int replay, int replay_scp,
+                double* scp_margins, double* pow_margins, double* pipg_margins) {
   const int nu = p->nu;
   orc_pd ws;
   orc_pd_alloc(&ws, N, nu);
@@ -1187,7 +1239,9 @@ int orc_solve(const orc_params* p, int N, const double* x0, double* X, double* U
     if (replay) { fp = trace[(j - 1) * 2 + 0]; fj = trace[(j - 1) * 2 + 1]; }
     int pit, jit;
     double sg, dfc, stp;
-    orc_scp_iterate(p, N, x0, X, U, &ws, fp, fj, 0.0, &sg, &pit, &jit, &dfc, &stp);
+    orc_scp_iterate_m(p, N, x0, X, U, &ws, fp, fj, 0.0, &sg, &pit, &jit, &dfc, &stp,
+                      pow_margins ? pow_margins + (size_t)(j - 1) * p->pow_jmax : NULL,
+                      pipg_margins ? pipg_margins + (size_t)(j - 1) * (p->pipg_jmax / p->pipg_jcheck) : NULL);
     if (trace && !replay) { trace[(j - 1) * 2 + 0] = pit; trace[(j - 1) * 2 + 1] = jit; }
     res->pipg_iters += jit;
     res->pow_iters += pit;
@@ -1196,6 +1250,9 @@ int orc_solve(const orc_params* p, int N, const double* x0, double* X, double* U
     if (!all_finite(N * NX, X) || !all_finite(N * nu, U)) { res->status = 2; break; }
     int conv = stp <= p->scp_eps_step && dfc <= p->scp_eps_defect &&
                (X[(N - 1) * NX + XY] - X[XY]) <= (N - 1) * p->eps_ctcs;
+    if (scp_margins)
+      scp_margins[j - 1] = maxd(maxd(margin(stp, p->scp_eps_step), margin(dfc, p->scp_eps_defect)),
+                                margin(X[(N - 1) * NX + XY] - X[XY], (N - 1) * p->eps_ctcs));
     res->status = conv ? 0 : 1;
     if (conv && !replay) break;
   }

@@ -127,6 +127,23 @@ double orc_power(const orc_params* p, const orc_qp* qp, const orc_pd* start, int
  * Returns the number of iterations run. */
 int orc_pipgc(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, int force_iters);
 
+/* Stop-decision report (test aid for checking another solver's stop decisions
+ * against the oracle's own).  Each test "a <= b" of the solver is reported as
+ * the relative margin (a - b) / b, which is <= 0 exactly when the test passes;
+ * a test of several conditions reports the largest margin.
+ *   orc_power_m:  margins[i]  = Alg. power's test after iteration i + 1
+ *   orc_pipgc_m:  margins[c]  = Alg. stopping at the check after iteration
+ *                 (c + 1) pipg_jcheck (iterates j and j - 1, unextrapolated)
+ * They are written for every iteration run, including under force_iters (the
+ * test is then evaluated but does not stop the loop); NULL skips the report.
+ * orc_stop_custom evaluates Alg. stopping on the iterate pair (a, b): returns
+ * 1 to terminate, and its margin in *m (may be NULL). */
+double orc_power_m(const orc_params* p, const orc_qp* qp, const orc_pd* start, int force_iters, int* iters,
+                   double* margins);
+int orc_pipgc_m(const orc_params* p, const orc_qp* qp, double sigma, orc_pd* ws, int force_iters,
+                double* margins);
+int orc_stop_custom(const orc_params* p, const orc_qp* qp, const orc_pd* a, const orc_pd* b, double* m);
+
 /* Dense canonical QP (Eq. canonical-QP / parsed-data) and generic PIPG (Alg. 1). */
 int  orc_qp_dim(int N, int nu);  /* n_z */
 void orc_qp_dense(const orc_qp* qp, double* P, double* pv, double* G, double* gv,
@@ -164,6 +181,13 @@ int orc_scp_iterate(const orc_params* p, int N, const double* x0, double* X, dou
                     orc_pd* ws, int force_pow, int force_pipg, double force_sigma,
                     double* sigma, int* pow_it, int* pipg_it, double* defect, double* step);
 
+/* orc_scp_iterate with the stop-decision report of its power iteration
+ * ([pow_jmax]) and PIPG loop ([pipg_jmax / pipg_jcheck]); either may be NULL. */
+int orc_scp_iterate_m(const orc_params* p, int N, const double* x0, double* X, double* U,
+                      orc_pd* ws, int force_pow, int force_pipg, double force_sigma,
+                      double* sigma, int* pow_it, int* pipg_it, double* defect, double* step,
+                      double* pow_margins, double* pipg_margins);
+
 /* Touchdown error 0.5 sum_{E_f} ((x_prop,N - z_f) / P_x)^2 of a trajectory,
  * x_prop,N the RK4 propagation of the last interval. */
 double orc_touchdown(const orc_params* p, int N, const double* X, const double* U);
@@ -173,6 +197,15 @@ double orc_touchdown(const orc_params* p, int N, const double* X, const double* 
  * forces those counts, and replay_scp forces the SCP iteration count. */
 int orc_solve(const orc_params* p, int N, const double* x0, double* X, double* U,
               orc_result* res, int* trace, int replay, int replay_scp);
+
+/* orc_solve with the stop-decision report of every SCP iteration j (0-based):
+ * scp_margins [scp_cap] the SCP convergence test (R8) after iteration j + 1,
+ * pow_margins [scp_cap][pow_jmax] and pipg_margins [scp_cap][pipg_jmax /
+ * pipg_jcheck] as for orc_scp_iterate_m; scp_cap = max(scp_jmax, replay_scp).
+ * Entries of iterations not run are left untouched.  Any may be NULL. */
+int orc_solve_m(const orc_params* p, int N, const double* x0, double* X, double* U,
+                orc_result* res, int* trace, int replay, int replay_scp,
+                double* scp_margins, double* pow_margins, double* pipg_margins);
 
 /* Batch over instances with OpenMP (nthreads <= 0: library default).
  * x0s: [B][NX-1], X: [B][Nmax][NX], U: [B][Nmax][nu]; N may differ per instance. */

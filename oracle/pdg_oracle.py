@@ -151,6 +151,12 @@ def lib(model: str = "6dof"):
             L.orc_touchdown.argtypes = [P, C.c_int, _DP, _DP]
             L.orc_touchdown.restype = C.c_double
             L.orc_solve.argtypes = [P, C.c_int, _DP, _DP, _DP, C.POINTER(Result), _IP, C.c_int, C.c_int]
+            L.orc_solve_m.argtypes = [P, C.c_int, _DP, _DP, _DP, C.POINTER(Result), _IP, C.c_int, C.c_int,
+                                      _DP, _DP, _DP]
+            L.orc_pipgc_m.argtypes = [P, C.POINTER(QP), C.c_double, C.POINTER(PD), C.c_int, _DP]
+            L.orc_pipgc_m.restype = C.c_int
+            L.orc_stop_custom.argtypes = [P, C.POINTER(QP), C.POINTER(PD), C.POINTER(PD), _DP]
+            L.orc_stop_custom.restype = C.c_int
             L.orc_solve_batch.argtypes = [P, C.c_int, C.c_int, _IP, _DP, _DP, _DP, _DP, _DP, _IP, _IP,
                                           C.POINTER(C.c_longlong), C.c_int]
             _libs[model] = L
@@ -350,11 +356,26 @@ def power(p, qp: QPData, start: PDState, force_iters: int = 0):
     return sig, it.value
 
 
-def pipgc(p, qp: QPData, sigma: float, ws: PDState, force_iters: int = 0) -> int:
-    """Runs Alg. PIPG_custom in place on ws; returns the iteration count."""
+def pipgc(p, qp: QPData, sigma: float, ws: PDState, force_iters: int = 0, margins: bool = False):
+    """Runs Alg. PIPG_custom in place on ws; returns the iteration count, and
+    with margins=True also the stop test's margin at every check (NaN where
+    no check ran; see orc_pipgc_m)."""
     qs = qp.cstruct()
     ss = ws.cstruct()
-    return _L(p).orc_pipgc(C.byref(make_params(p)), C.byref(qs), float(sigma), C.byref(ss), int(force_iters))
+    if not margins:
+        return _L(p).orc_pipgc(C.byref(make_params(p)), C.byref(qs), float(sigma), C.byref(ss), int(force_iters))
+    m = np.full(max(int(p["pipg_jmax"]), int(force_iters)) // int(p["pipg_jcheck"]), np.nan)
+    n = _L(p).orc_pipgc_m(C.byref(make_params(p)), C.byref(qs), float(sigma), C.byref(ss), int(force_iters), _d(m))
+    return n, m
+
+
+def stop_custom(p, qp: QPData, a: PDState, b: PDState):
+    """Alg. stopping on the iterate pair (a, b): (terminate?, margin)."""
+    m = C.c_double()
+    qs = qp.cstruct()
+    r = _L(p).orc_stop_custom(C.byref(make_params(p)), C.byref(qs), C.byref(a.cstruct()), C.byref(b.cstruct()),
+                              C.byref(m))
+    return bool(r), m.value
 
 
 def qp_dim(N, nu, model: str = "6dof"):
@@ -449,19 +470,33 @@ def final_iteration_outputs(p, x0, X, U, ws: PDState, sigma, n_pipg):
     return X[0, 0] - X[-1, 0], touchdown(p, X, U)
 
 
-def solve(p, N, x0, trace: Optional[np.ndarray] = None, replay_scp: int = 0):
+def solve(p, N, x0, trace: Optional[np.ndarray] = None, replay_scp: int = 0, margins: bool = False):
     """Full SCP solve of one instance.  With replay_scp > 0, trace[j] = (power
-    iterations, PIPG iterations) of SCP iteration j is replayed exactly."""
+    iterations, PIPG iterations) of SCP iteration j is replayed exactly.
+    margins=True adds the oracle's own stop-test margins (orc_solve_m):
+    "scp_margin" [scp_iters], "pow_margin" [scp_iters][pow_jmax] and
+    "pipg_margin" [scp_iters][pipg_jmax // pipg_jcheck], NaN where no test ran."""
     nu, NX = int(p["nu"]), nx_of(p)
     X = np.zeros((N, NX)); U = np.zeros((N, nu))
     res = Result()
     jm = max(int(p["scp_jmax"]), int(replay_scp))
     tr = np.zeros((jm, 2), np.int32) if trace is None else np.ascontiguousarray(trace, np.int32)
-    _L(p).orc_solve(C.byref(make_params(p)), int(N), _d(np.ascontiguousarray(x0, np.float64)), _d(X), _d(U),
-                    C.byref(res), _i(tr), 1 if replay_scp > 0 else 0, int(replay_scp))
-    return dict(X=X, U=U, tf=res.tf, fuel=res.fuel, status=res.status, scp_iters=res.scp_iters,
-                pipg_iters=res.pipg_iters, pow_iters=res.pow_iters, defect=res.defect, step=res.step,
-                trace=tr[:res.scp_iters].copy())
+    args = (C.byref(make_params(p)), int(N), _d(np.ascontiguousarray(x0, np.float64)), _d(X), _d(U),
+            C.byref(res), _i(tr), 1 if replay_scp > 0 else 0, int(replay_scp))
+    if margins:
+        ms = np.full(jm, np.nan)
+        mp = np.full((jm, int(p["pow_jmax"])), np.nan)
+        mj = np.full((jm, int(p["pipg_jmax"]) // int(p["pipg_jcheck"])), np.nan)
+        _L(p).orc_solve_m(*args, _d(ms), _d(mp), _d(mj))
+    else:
+        _L(p).orc_solve(*args)
+    out = dict(X=X, U=U, tf=res.tf, fuel=res.fuel, status=res.status, scp_iters=res.scp_iters,
+               pipg_iters=res.pipg_iters, pow_iters=res.pow_iters, defect=res.defect, step=res.step,
+               trace=tr[:res.scp_iters].copy())
+    if margins:
+        n = res.scp_iters
+        out.update(scp_margin=ms[:n].copy(), pow_margin=mp[:n].copy(), pipg_margin=mj[:n].copy())
+    return out
 
 
 def solve_batch(p, x0s, Ns, Nmax=None, nthreads=0):

@@ -16,28 +16,51 @@ def _fine_defects(O, p, X, U, nsub=200):
     return np.array(out)
 
 
-def _dense_g(O, p, X, U, nsamp=40):
+def _dense_g(O, p, X, U, nsamp=40, integral=False):
+    """g at nsamp + 1 points of every interval along the flow from each node
+    (FOH controls).  integral=True also returns, per interval, the flow's
+    change of the CTCS state y and the trapezoid sum of its integrand
+    s sum_i max(0, g_i)^2 over the same points."""
     N, nu = U.shape
-    gs = []
+    gs, ys = [], []
     for k in range(N - 1):
         x = X[k].copy()
         uk, uk1 = U[k].copy(), U[k + 1].copy()
-        for i in range(nsamp):
+        vals = []
+        for i in range(nsamp + 1):
             lp = i / nsamp
             u = (1 - lp) * U[k] + lp * U[k + 1]
-            gs.append(O.g(p, x, u))
+            gi = O.g(p, x, u)
+            if i < nsamp:
+                gs.append(gi)
+            vals.append(u[-1] * np.sum(np.maximum(gi, 0.0) ** 2))
+            if i == nsamp:
+                break
             a = uk * (1 - lp) + uk1 * lp
             b = uk * (1 - lp - 1 / nsamp) + uk1 * (lp + 1 / nsamp)
             a[-1] /= (N - 1) * nsamp; b[-1] /= (N - 1) * nsamp
             x = O.flow(p, x, a, b, 20)
-    return np.array(gs)
+        h = 1.0 / ((N - 1) * nsamp)
+        ys.append((x[-1] - X[k, -1], h * (np.sum(vals) - 0.5 * (vals[0] + vals[-1]))))
+    return (np.array(gs), np.array(ys)) if integral else np.array(gs)
 
 
-@pytest.mark.parametrize("nu", [4, 7])
-def test_converged_solution_is_feasible(oracle, inputs, nu):
+@pytest.mark.parametrize("nu,seed", [(4, 21), (4, 23), (7, 21)])
+def test_converged_solution_is_feasible(oracle, inputs, nu, seed):
+    """At convergence (reading R8) the trajectory meets, in continuous time:
+    - the dynamics: the scaled defect against a 200-substep flow is within the
+      solver's own defect tolerance scp_eps_defect (the 10-substep RK4 the
+      solver uses differs from the fine flow by far less);
+    - the unit quaternion: the flow preserves ||q|| (Omega(w) is skew, Sec. 5),
+      so ||q_k|| - 1 can only come from the defects of the nodes before k;
+    - the CTCS budget: y_N - y_1 <= (N - 1) eps, and the flow's y agrees with
+      a trapezoid sum of s sum_i max(0, g_i)^2 at 41 points per interval (so
+      the integrator state integrates the path constraints, Eq.
+      sys-dyn-dil-aug); the solve's own y_N - y_1 is that integral to 10 %;
+    - non-increasing mass, the boundary conditions and the dilation box."""
     p = inputs.load_params(nu=nu)
     N = 15
-    x0 = inputs.dispersion(p, 1, 21, "bj")[0]
+    x0 = inputs.dispersion(p, 1, seed, "bj")[0]
     r = oracle.solve(p, N, x0)
     assert r["status"] == 0, r
     X, U = r["X"], r["U"]
@@ -47,11 +70,16 @@ def test_converged_solution_is_feasible(oracle, inputs, nu):
     fx = p["fix_f"].astype(bool)
     np.testing.assert_allclose(X[-1][fx], p["z_f"][fx], atol=1e-9)
     d = _fine_defects(oracle, p, X, U)
-    assert d[:, :14].max() < 2e-3, d.max()
-    assert X[-1, 14] - X[0, 14] <= (N - 1) * p["eps_ctcs"] + 1e-9
-    np.testing.assert_allclose(np.linalg.norm(X[:, 7:11], axis=1), 1.0, atol=5e-3)
-    assert np.all(np.diff(X[:, 0]) <= 1e-6)
-    g = _dense_g(oracle, p, X, U)
+    assert d[:, :14].max() <= p["scp_eps_defect"], d.max()
+    dq = np.concatenate([[0.0], np.cumsum(np.linalg.norm(d[:, 7:11] * p["P_x"][7:11], axis=1))])
+    assert np.all(np.abs(np.linalg.norm(X[:, 7:11], axis=1) - 1.0) <= dq + 1e-12)
+    assert np.all(np.diff(X[:, 0]) <= 0.0)
+    g, ys = _dense_g(oracle, p, X, U, integral=True)
+    budget = (N - 1) * p["eps_ctcs"]
+    assert X[-1, 14] - X[0, 14] <= budget + 1e-12
+    flow_dy, quad = ys[:, 0].sum(), ys[:, 1].sum()
+    assert abs(flow_dy - quad) <= 0.1 * quad + 1e-10, (flow_dy, quad)
+    assert abs((X[-1, 14] - X[0, 14]) - flow_dy) <= 0.1 * flow_dy + 1e-10
     assert np.maximum(g, 0).max() < 0.05
     assert np.all(U[:, -1] >= p["s_min"] - 1e-9) and np.all(U[:, -1] <= p["s_max"] + 1e-9)
     tf = np.sum(0.5 * (U[:-1, -1] + U[1:, -1])) / (N - 1)
