@@ -171,3 +171,18 @@ def test_scp_map_is_not_contractive_at_convergence(oracle, inputs, model, N):
                    - _scp_map(oracle, p, x0, z0 - e, X, U, ws, sig, n)) / (2 * e[j])
     rho = np.abs(np.linalg.eigvals(J * scale[None, :] / scale[:, None])).max()
     assert rho >= 0.99, rho
+
+
+def test_scp_creeps_at_tight_tolerance(oracle, inputs):
+    """The total derivative through the SCP fixed point would need solves
+    converged to that fixed point, e.g. to check it against differences of
+    whole solves.  At a step tolerance of 1e-8 (PIPG converged to 1e-10 in
+    every subproblem) the prox-linear iteration with its fixed prox weight
+    does not get there: after 300 SCP iterations its scaled step is still
+    above 1e-4, creeping down far slower than linearly."""
+    p = inputs.load_params(model="3dof", scp_eps_step=1e-8, scp_eps_defect=1e-10, scp_jmax=300,
+                           pipg_eps_rel=1e-10, pipg_eps_abs=1e-13, pipg_jmax=20000)
+    x0 = inputs.dispersion(p, 1, 3, "bj")[0]
+    r = oracle.solve(p, 10, x0)
+    assert r["status"] == 1 and r["scp_iters"] == 300
+    assert r["step"] > 1e-4 and r["defect"] < 1e-6
