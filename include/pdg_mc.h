@@ -2,7 +2,7 @@
  * pdg_mc.h -- C ABI of the batched GB300 solver for Monte Carlo 6-DoF
  * powered-descent guidance (arXiv 2404.18034).
  *
- * Each instance is a free-final-time 6-DoF landing problem (Sec. 5) solved by
+ * Each instance is a free-final-time 6-DoF landing problem (Sec. 4) solved by
  * prox-linear sequential convex programming (Sec. 2.3, Eq. cvx-subproblem)
  * with the CTCS reformulation (Sec. 2.1, Eq. sys-dyn-dil-aug).  Every SCP
  * iteration discretizes the augmented dynamics with their state-transition
@@ -14,7 +14,7 @@
  * boundary conditions, Mayer cost) is instantiated by a model fixed when the
  * library is compiled, and every entry point below has the same meaning in
  * each library:
- *   libpdg_mc.so       the 6-DoF model of Sec. 5, state size NX = 15;
+ *   libpdg_mc.so       the 6-DoF model of Sec. 4, state size NX = 15;
  *   libpdg_mc_3dof.so  the translational 3-DoF model, NX = 8: the 6-DoF model
  *                      without attitude, thrust in the inertial frame, nu = 4,
  *                      path rows m_dry, altitude, v_max, thrust pointing within
@@ -64,7 +64,7 @@ extern "C" {
 #define PDG_BUDGET 3      /* the device-side wall-clock budget ran out */
 #define PDG_BAD_INPUT 4   /* n_nodes out of range or non-finite x0 */
 
-/* Problem and solver parameters; angles in radians.  Sec. 5 lists the model
+/* Problem and solver parameters; angles in radians.  Sec. 4 lists the model
  * quantities, Sec. 2.3.2 the scalings P_x, P_u and Sec. 3 the PIPG inputs. */
 typedef struct pdg_params {
   int nu;                 /* 4 or 7 */
@@ -94,7 +94,7 @@ typedef struct pdg_params {
                              projection step) instead of CTCS rows; needs P_u equal on
                              the three thrust components; no gradients */
   int glide_slope;        /* 1: add the glide-slope row tan^2(gamma_gs) (r_y^2 + r_z^2) - r_x^2
-                             <= 0 to g (CTCS), the bound gamma_gs named in Sec. 5 */
+                             <= 0 to g (CTCS), the bound gamma_gs named in Sec. 4 */
   double gamma_gs;        /* glide-slope angle from the horizontal (rad), in (0, pi/2) */
   double dt_min, dt_max, tf_max;  /* Sec. 2.2 time bounds, 0 = off: imposed as the node box
                              s_k in [dt_min (N-1), min(dt_max (N-1), tf_max)] on the
@@ -174,16 +174,17 @@ int pdg_mc_scp_step(pdg_handle* h, int B, const double* x0, const int* n_nodes,
                     double* phi, double* th, const int* force,
                     double* sigma, double* defect, double* step, int* iters, void* cuda_stream);
 
-/* Gradients of the converged outputs with respect to the initial state and
- * wet mass (FP64 handles only).  Solves the batch (persistent form), then
- * differentiates the solve's last SCP iteration as a function of x0 -- the
+/* One-step gradients of the converged outputs with respect to the initial
+ * state and wet mass (FP64 handles only).  Solves the batch (persistent form),
+ * then differentiates the solve's last SCP iteration as a function of x0 -- the
  * reference's first node moving with x0, the rest of that iteration's
  * reference, its PIPG warm start, step size and iteration count held --
  * through the RK4 discretization of the first interval (Sec. 2.3.1, forward
  * mode), the prescaling (Sec. 2.3.2) and the final PIPG_custom loop (reverse
  * mode, recomputed from checkpoints every 50 iterations, projections masked as
  * in the forward pass).  The paper has no gradient; this definition is the
- * solver's own.  Device buffers:
+ * solver's own.  It is not the total derivative through the SCP fixed point:
+ * the earlier iterations' dependence on x0 is not followed.  Device buffers:
  *   dL_dfuel, dL_dtouch [B]  upstream cotangents (NULL = zero)
  *   grad_x0 [B][NX-1]        d L / d x0 (6-DoF: m_wet, r, v, q, w), with
  *                            L = dL_dfuel fuel + dL_dtouch touchdown
@@ -227,7 +228,7 @@ int pdg_mc_set_threads(pdg_handle* h, int threads);
 int pdg_mc_autotune(pdg_handle* h, int B, const double* x0, const int* n_nodes, int mode, int* threads_out,
                     int* form_out, double* solves_per_s, void* cuda_stream);
 
-/* Choose how the PIPG loop (Alg. PIPG_custom, Sec. 4.3) is laid out on the
+/* Choose how the PIPG loop (Alg. PIPG_custom, Sec. 3) is laid out on the
  * CTA.  Results agree to rounding; only speed differs.
  *   form 1: blocks hat A^-, hat B^+- and the iterates in shared memory, any
  *           thread count (one thread per block row or column, looped);
@@ -260,10 +261,17 @@ int pdg_mc_pipg_form(const pdg_handle* h);
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream
  *     capture on that device.
+ *   - Under CUDA's lazy module loading (the default since CUDA 12) the
+ *     library's kernels and this array are put on a device at their first
+ *     use there.  If this entry point is that first use, its first call does
+ *     that loading, which takes the 32 MiB and the code's memory.  Callers
+ *     that must not allocate at all make one call (or one solve of any kind)
+ *     during set-up; every later call allocates nothing.
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (other streams, other threads) race and corrupt each other.  Serialize
  *     them, e.g. on one stream.
- * No cudaMalloc, cudaFree or other allocating call is made. */
+ * Apart from that first loading, no cudaMalloc, cudaFree or other allocating
+ * call is made. */
 int pdg_mc_solve_batch_noalloc(pdg_handle* h, int B, const double* x0, const int* n_nodes,
                                double* X, double* U, double* tf, double* fuel, int* status,
                                int* scp_iters, long long* pipg_iters, void* cuda_stream);
@@ -281,7 +289,7 @@ int pdg_mc_probe_fma(int precision, double* tflops, void* cuda_stream);
  * FP64 pipe).  PDG_EINVAL for other arguments.  Synchronizes the stream. */
 int pdg_mc_probe_fma_lanes(int precision, int active_lanes, double* ms, void* cuda_stream);
 
-/* State size NX of the library's model (15: 6-DoF of Sec. 5; 8: 3-DoF).
+/* State size NX of the library's model (15: 6-DoF of Sec. 4; 8: 3-DoF).
  * Needs no device and no handle; the binding checks it against the model it
  * expects before any call. */
 int pdg_mc_model_nx(void);

@@ -2,7 +2,7 @@
  * pdg_oracle.c -- TEST INFRASTRUCTURE ONLY (see pdg_oracle.h).
  *
  * Plain, serial, dense FP64 restatement of arXiv 2404.18034:
- *   Sec. 5      6-DoF dynamics F and path constraints g
+ *   Sec. 4      6-DoF dynamics F and path constraints g
  *   Sec. 2.1    time dilation and CTCS augmentation (Eq. sys-dyn-dil-aug)
  *   Sec. 2.2    uniform grid, FOH controls, multiple shooting (Eq. disc-dyn)
  *   Sec. 2.3.1  STM ODEs giving A_k, B^-_k, B^+_k (integrated with RK4 here)
@@ -25,7 +25,7 @@
  *      extrapolated dual of the dynamics rows; superscripts j of the first
  *      node read j+1.  Alg. power: v_k reads theta_k and sigma* accumulates
  *      from sigma* (not sigma); it acts on the full [G; H_y].
- *  R6  the dilation box is the only control box (Sec. 5); H of the canonical
+ *  R6  the dilation box is the only control box (Sec. 4); H of the canonical
  *      QP holds only the CTCS rows, the box and mu >= 0 are projections.
  *  R7  power iteration starts from the warm-start primal, or from all ones
  *      when that is zero; PIPG stop test compares iterates j+1 and j, with
@@ -42,7 +42,7 @@
 
 /* The problem template of Sec. 2 (F, g, boundary conditions, Mayer cost) is
  * instantiated by a model chosen when this file is compiled:
- *   default          the 6-DoF model of Sec. 5, x = (m, r, v, q, omega, y);
+ *   default          the 6-DoF model of Sec. 4, x = (m, r, v, q, omega, y);
  *   ORC_MODEL_3DOF   the translational (3-DoF) model Sec. 1 contrasts it with,
  *                    x = (m, r, v, y): point mass, thrust in the inertial
  *                    frame, no attitude (readings R18-R19).
@@ -59,7 +59,7 @@ enum { XM = 0, XR = 1, XV = 4, XQ = 7, XW = 11, XY = 14 };
 int orc_nx(void) { return NX; }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 5: model                                                             */
+/* Sec. 4: model                                                             */
 /* ------------------------------------------------------------------------ */
 
 /* C_{I<-B}(q), Hamilton scalar-first (R1). */
@@ -127,7 +127,7 @@ static void cross(const double* a, const double* b, double* c) {
 
 static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
-/* F(xi, zeta) of Sec. 5 (time domain, 14 rows). */
+/* F(xi, zeta) of Sec. 4 (time domain, 14 rows). */
 void orc_F(const orc_params* p, const double* x, const double* u, double* Fx) {
   const double m = x[XM];
   const double* v = x + XV;
@@ -160,7 +160,7 @@ void orc_F(const orc_params* p, const double* x, const double* u, double* Fx) {
   for (int i = 0; i < 3; i++) Fx[11 + i] = (rxT[i] - wxJw[i] + gam[i]) / p->J_B[i];
 }
 
-/* g(xi, zeta) of Sec. 5 with the tilt reading R2.  nu = 4 drops the gamma row. */
+/* g(xi, zeta) of Sec. 4 with the tilt reading R2.  nu = 4 drops the gamma row. */
 int orc_g(const orc_params* p, const double* x, const double* u, double* g) {
   const double* r = x + XR;
   const double* v = x + XV;
@@ -182,7 +182,7 @@ int orc_g(const orc_params* p, const double* x, const double* u, double* g) {
     const double* gm = u + 3;
     g[ng++] = dot3(gm, gm) - p->gamma_max * p->gamma_max;
   }
-  /* glide slope (parameter gamma_gs of Sec. 5; its row is not printed): the
+  /* glide slope (parameter gamma_gs of Sec. 4; its row is not printed): the
      vehicle stays in the cone tan(gamma_gs) ||(r_y, r_z)|| <= r_x about the
      inertial up axis through the landing site.  Written squared,
      tan^2 (r_y^2 + r_z^2) - r_x^2 <= 0, which with the altitude row r_x >= 0
@@ -548,7 +548,7 @@ void orc_scale(const orc_params* p, int N, const double* x0, const double* X, co
     /* hat eps_k = eps E_y P_x^{-1} E_y^T - E_y P_x^{-1} (xbar_{k+1} - xbar_k) */
     qp->eps[k] = p->eps_ctcs / Px[XY] - (X[(k + 1) * NX + XY] - X[k * NX + XY]) / Px[XY];
   }
-  /* control box on the dilation factor only (Sec. 5, R6).  The time bounds
+  /* control box on the dilation factor only (Sec. 4, R6).  The time bounds
      of Sec. 2.2 tighten it node-wise: with FOH s, Delta t_k = (s_k + s_{k+1})
      / (2 (N-1)) lies between the node values / (N-1), and t_f = sum Delta t_k
      is at most max_k s_k, so s_k in [dt_min (N-1), min(dt_max (N-1), tf_max)]
@@ -1096,7 +1096,7 @@ double orc_sym_eig_max(int n, double* M) {
 /* ------------------------------------------------------------------------ */
 
 #ifndef ORC_MODEL_3DOF
-/* Initial guess (Sec. 5 asks for "an appropriate" one; this reading):
+/* Initial guess (Sec. 4 asks for "an appropriate" one; this reading):
  * straight lines in r, v, omega from x0 to z_f; normalized linear
  * interpolation of q from x0 to z_f; mass linear from m_wet to
  * (m_wet + m_dry)/2; y = 0; hover thrust m ||g|| along body x; gamma = 0;

@@ -14,11 +14,11 @@
  *
  * The model (F, g and the initial guess of the problem template of Sec. 2)
  * is chosen when the library is compiled: libpdg_oracle.so holds the 6-DoF
- * model of Sec. 5, libpdg_oracle_3dof.so (-DORC_MODEL_3DOF) the translational
+ * model of Sec. 4, libpdg_oracle_3dof.so (-DORC_MODEL_3DOF) the translational
  * 3-DoF model.  orc_nx() returns the library's state size NX.
  *
  * Layouts (row-major, double):
- *   6-DoF state x[15] = (m, r[3], v[3], q[4], omega[3], y)   (Sec. 2.1, Sec. 5)
+ *   6-DoF state x[15] = (m, r[3], v[3], q[4], omega[3], y)   (Sec. 2.1, Sec. 4)
  *   3-DoF state x[8]  = (m, r[3], v[3], y)
  *   control u[nu] = (T[3], [gamma[3],] s), nu in {4, 7}; the 3-DoF model has nu = 4
  *   X[N][NX], U[N][nu]; A[N-1][NX][NX]; Bm, Bp[N-1][NX][nu]; xprop[N-1][NX]
@@ -79,7 +79,7 @@ typedef struct orc_qp {
   double zf[15];
   int fixf[15];
   double w_cost, w_prox, w_ep;
-  double ecost[15]; /* e_cost on the scaled x_N (Sec. 4 objective) */
+  double ecost[15]; /* e_cost on the scaled x_N (Eq. cvx-subproblem-custom objective) */
   int soc;          /* thrust sector projection on (see orc_params.soc_thrust) */
   double *Tbar;     /* [N][3] reference thrust (unscaled) */
   double soc_Tmax, soc_tan, soc_PT;
@@ -95,20 +95,20 @@ typedef struct orc_pd {
   double *th;   /* [N-1] */
 } orc_pd;
 
-/* ---- model (Sec. 5) ---- */
+/* ---- model (Sec. 4) ---- */
 int  orc_nx(void);                                                                /* NX */
 void orc_F(const orc_params* p, const double* x, const double* u, double* Fx);   /* dxi/dt, NX - 1 */
 int  orc_g(const orc_params* p, const double* x, const double* u, double* g);    /* returns n_g */
 void orc_f(const orc_params* p, const double* x, const double* u, double* f);    /* Eq. sys-dyn-dil-aug, NX */
 void orc_jac(const orc_params* p, const double* x, const double* u, double* A, double* B);
 
-/* ---- discretization (Sec. 3.2, Sec. 3.3.1) ---- */
+/* ---- discretization (Sec. 2.2, Sec. 2.3.1) ---- */
 void orc_flow(const orc_params* p, const double* xk, const double* uk, const double* uk1,
               int nsub, double* xout);
 void orc_discretize(const orc_params* p, int N, const double* X, const double* U,
                     double* A, double* Bm, double* Bp, double* xprop);
 
-/* ---- scaled subproblem (Sec. 3.3.2) ---- */
+/* ---- scaled subproblem (Sec. 2.3.2) ---- */
 int  orc_qp_alloc(orc_qp* qp, int N, int nu);
 void orc_qp_free(orc_qp* qp);
 void orc_scale(const orc_params* p, int N, const double* x0, const double* X, const double* U,
@@ -119,7 +119,7 @@ void orc_pd_free(orc_pd* s);
 void orc_pd_zero(orc_pd* s, int N, int nu);
 void orc_pd_copy(orc_pd* dst, const orc_pd* src, int N, int nu);
 
-/* ---- solver (Sec. 4) ---- */
+/* ---- solver (Sec. 3) ---- */
 /* Alg. power.  force_iters > 0 runs exactly that many iterations. Returns sigma. */
 double orc_power(const orc_params* p, const orc_qp* qp, const orc_pd* start, int force_iters, int* iters);
 /* Alg. PIPG_custom + Alg. stopping.  ws is warm start in / solution out.
@@ -161,7 +161,7 @@ void orc_sector_project(double* T, double Tmax, double tan_delta);
 /* Jacobi eigenvalues of a dense symmetric matrix (in place; returns the largest). */
 double orc_sym_eig_max(int n, double* M);
 
-/* ---- SCP (Sec. 3.3) ---- */
+/* ---- SCP (Sec. 2.3) ---- */
 void orc_init_guess(const orc_params* p, int N, const double* x0, double* X, double* U);
 
 typedef struct orc_result {

@@ -2,7 +2,7 @@
 
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this module.  It builds ``libpdg_oracle.so`` (the
-6-DoF model of Sec. 5) and ``libpdg_oracle_3dof.so`` (the translational 3-DoF
+6-DoF model of Sec. 4) and ``libpdg_oracle_3dof.so`` (the translational 3-DoF
 model) from ``pdg_oracle.c`` with gcc and exposes the oracle's routines on
 numpy arrays; every routine picks the library by the parameter dict's
 ``model`` ("6dof" when absent), and state arrays have that model's size NX.

@@ -1,7 +1,7 @@
 """Build the CUDA libraries in-tree for sm_103a (GB300) with nvcc.
 
 One library per model of the problem template (the model is a compile-time
-choice of csrc/pdg_device.cuh): libpdg_mc.so holds the 6-DoF model of Sec. 5,
+choice of csrc/pdg_device.cuh): libpdg_mc.so holds the 6-DoF model of Sec. 4,
 libpdg_mc_3dof.so the translational 3-DoF model.  Both compile from the same
 sources, in parallel.  build_model() compiles a library for a model header of
 the caller's (the interface is listed in csrc/pdg_device.cuh).

@@ -1,6 +1,6 @@
 // pdg_device.cuh -- device side of the batched solver: parameters, the
 // per-instance shared-memory layout, the choice of the model (the 6-DoF model
-// of Sec. 5, the 3-DoF model, or a caller's header) and block reductions
+// of Sec. 4, the 3-DoF model, or a caller's header) and block reductions
 // (arXiv 2404.18034, Sec. 2-5).  One CTA owns one instance at a time; every
 // block of its subproblem lives in shared memory.
 #pragma once
@@ -50,7 +50,7 @@ struct Lay {
 
 // The model -- F, g, their compact Jacobians and the initial guess of one
 // instance of the problem template of Sec. 2 -- is chosen when the library is
-// compiled: the 6-DoF model of Sec. 5 by default, the translational 3-DoF
+// compiled: the 6-DoF model of Sec. 4 by default, the translational 3-DoF
 // model with PDG_MODEL_3DOF, or a model of the caller's with
 // PDG_MODEL_HEADER="<path>".  A model header defines, in namespace pdg:
 //   NX          state size; the CTCS integrator y is the last state (IY = NX-1)

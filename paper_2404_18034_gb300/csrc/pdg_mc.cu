@@ -1,6 +1,6 @@
 // pdg_mc.cu -- kernels and C ABI of the batched GB300 solver for Monte Carlo
 // powered-descent guidance (arXiv 2404.18034).  See include/pdg_mc.h.  The
-// model (6-DoF of Sec. 5, or 3-DoF with PDG_MODEL_3DOF) is fixed at compile
+// model (6-DoF of Sec. 4, or 3-DoF with PDG_MODEL_3DOF) is fixed at compile
 // time by pdg_device.cuh; nothing in this file depends on which.
 //
 // Two execution forms share the device phases of pdg_phases.cuh:

@@ -1,6 +1,6 @@
 // pdg_model_3dof.cuh -- the translational (3-DoF) powered-descent model as a
 // second instance of the problem template of Sec. 2 of arXiv 2404.18034: the
-// 6-DoF model of Sec. 5 without attitude.  State x = (m, r, v, y), controls
+// 6-DoF model of Sec. 4 without attitude.  State x = (m, r, v, y), controls
 // (T, s) with T in the inertial frame:
 //   m' = -alpha ||T||,  r' = v,  v' = T / m + g,
 // path constraints (rows of g): m_dry - m, -r_x, ||v||^2 - v_max^2, the

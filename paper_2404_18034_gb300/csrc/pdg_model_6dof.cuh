@@ -1,4 +1,4 @@
-// pdg_model_6dof.cuh -- the 6-DoF powered-descent model of Sec. 5 of arXiv
+// pdg_model_6dof.cuh -- the 6-DoF powered-descent model of Sec. 4 of arXiv
 // 2404.18034 as an instance of the problem template of Sec. 2: state
 // x = (m, r, v, q, omega, y), controls (T, [gamma,] s).  Included by
 // pdg_device.cuh after DParams; see there for the model interface.
@@ -16,7 +16,7 @@ constexpr int SA_A = 42;
 #define PDG_MODEL_USES_INERTIA 1
 
 // ---------------------------------------------------------------------------
-// Sec. 5 model.  One call evaluates, at (x, u): f = s (F, sum |g|_+^2), the
+// Sec. 4 model.  One call evaluates, at (x, u): f = s (F, sum |g|_+^2), the
 // nonzero pattern of df/dx in compact form, and df/du densely (15 x NU).
 // Compact A layout (SA_A slots):
 //   [0]  s           (r rows wrt v)
@@ -220,7 +220,7 @@ __device__ __forceinline__ void model_vjp(const double* A, const double* Bd, con
 }
 
 // Initial guess at node fraction t = (k-1)/(N-1) (the paper asks for "an
-// appropriate" one; Sec. 5): straight lines in r, v, w from x0 to z_f,
+// appropriate" one; Sec. 4): straight lines in r, v, w from x0 to z_f,
 // normalized linear interpolation of q, mass from m_wet to (m_wet + m_dry)/2,
 // y = 0, hover thrust m|g| along body x, gamma = 0, s = tf_guess.
 template <typename R, int NU>

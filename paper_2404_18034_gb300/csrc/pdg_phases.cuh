@@ -11,7 +11,7 @@ namespace pdg {
 __device__ __forceinline__ double max0(double x) { return __double_as_longlong(x) < 0 ? 0.0 : x; }
 __device__ __forceinline__ float max0(float x) { return __float_as_int(x) < 0 ? 0.0f : x; }
 
-// Initial guess of every node (Sec. 5 asks for "an appropriate" one; the
+// Initial guess of every node (Sec. 4 asks for "an appropriate" one; the
 // model's model_init_node says which).
 template <typename R, int NU>
 __device__ void phase_init_guess(const DParams& P, const Lay& L, R* sm) {

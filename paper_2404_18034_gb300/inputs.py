@@ -5,7 +5,7 @@ parameter set (plain numbers) and draws dispersed initial conditions from a
 counter-based generator, so that both sides of a parity check see the same
 inputs.  It imports neither the CUDA binding nor the oracle.
 
-State layout (Sec. 5 of arXiv 2404.18034): x = (m, r[3], v[3], q[4], w[3], y);
+State layout (Sec. 4 of arXiv 2404.18034): x = (m, r[3], v[3], q[4], w[3], y);
 the initial condition passed to a solve is the first 14 entries (m_wet, r, v,
 q, w).  Controls: (T[3], s) for nu = 4, (T[3], gamma[3], s) for nu = 7.  The
 translational 3-DoF model ("model": "3dof" in its parameter file) has
@@ -17,7 +17,7 @@ Dispersions:
              U(-2, 2) deg per time unit per axis; wet mass scaled by
              1 + U(-0.02, 0.02).  The 3-DoF model draws the same m, r, v.
   "paper256" r(0) ~ (U(6, 9), U(3, 6), U(1, 2)) with the rest nominal, the
-             Monte Carlo distribution of Sec. 7 of the paper.
+             Monte Carlo distribution of Sec. 6 of the paper.
 """
 from __future__ import annotations
 
@@ -83,7 +83,7 @@ def load_params(path: Optional[str] = None, nu: Optional[int] = None, model: Opt
     for k in ("pipg_jmax", "pipg_jcheck", "pow_jmax", "scp_jmax", "rk4_substeps"):
         p[k] = int(raw[k])
     p["soc_thrust"] = int(raw.get("soc_thrust", 0))
-    # glide slope (gamma_gs of Sec. 5, from the horizontal) and the Sec. 2.2
+    # glide slope (gamma_gs of Sec. 4, from the horizontal) and the Sec. 2.2
     # time bounds (0 = off); off in the default workloads
     p["glide_slope"] = int(raw.get("glide_slope", 0))
     p["dt_min"] = float(raw.get("dt_min", 0.0))

@@ -165,7 +165,7 @@ def test_variants_match_oracle_replay(torch_cuda, oracle, inputs, ov):
 
 
 def test_paper_distribution_sampled(torch_cuda, oracle, inputs):
-    """The paper's r(0) distribution (Sec. 7) on the 3-DoF model: 256
+    """The paper's r(0) distribution (Sec. 6) on the 3-DoF model: 256
     instances, statuses of all within the oracle's convergence share, values
     of a sample against the replay."""
     torch = torch_cuda

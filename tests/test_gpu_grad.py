@@ -38,7 +38,7 @@ def _fd(oracle, p, x0, X, U, ws, sig, n, h=1e-6):
                                         (4, 11, 3, {"model": "3dof", "glide_slope": 1}),
                                         (4, 10, 3, {"pipg_form": 2})])
 def test_gradient_matches_oracle_finite_differences(torch_cuda, oracle, inputs, nu, N, B, ov):
-    """Both models: the 6-DoF one of Sec. 5 and the 3-DoF instance of the
+    """Both models: the 6-DoF one of Sec. 4 and the 3-DoF instance of the
     template (gradient d L / d (m_wet, r, v) there).  With the shared-memory
     PIPG form the solve records the last PIPG loop's checkpoints for the
     adjoint; with the register form (pipg_form 2) the adjoint reruns that

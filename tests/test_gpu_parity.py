@@ -447,13 +447,13 @@ def test_fp32_error_report_n30(torch_cuda, oracle, inputs):
 
 
 def test_paper_model_paper256_distribution(torch_cuda, oracle, inputs):
-    """The paper's model (nu = 7, RCS torque) on the Monte Carlo of Sec. 7
-    (tests/golden/paper_sec7_monte_carlo.json: 256 runs, SCP <= 25, PIPG
+    """The paper's model (nu = 7, RCS torque) on the Monte Carlo of Sec. 6
+    (tests/golden/paper_sec6_monte_carlo.json: 256 runs, SCP <= 25, PIPG
     2500, all converge in the paper): the runs converge and sampled ones
     match the oracle replay."""
     import json
     import os
-    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_sec7_monte_carlo.json")) as fh:
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_sec6_monte_carlo.json")) as fh:
         mc = json.load(fh)
     torch = torch_cuda
     p = inputs.load_params(nu=7, scp_jmax=mc["scp_iteration_limit"], pipg_jmax=mc["pipg_iterations_per_subproblem"])

@@ -2,7 +2,7 @@
 translational 3-DoF powered-descent model (x = (m, r, v, y), inertial thrust).
 
 The pins come from outside the oracle: the rocket equation integrated in
-closed form under a constant inertial thrust, the 6-DoF model of Sec. 5 (a
+closed form under a constant inertial thrust, the 6-DoF model of Sec. 4 (a
 separately pinned library) at level attitude and zero rate, central
 differences, the dense canonical QP of Eq. parsed-data with Alg. 1, KKT
 conditions, and an impulse bound that every feasible trajectory obeys."""

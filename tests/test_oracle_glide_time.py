@@ -1,5 +1,5 @@
 """Pins of the oracle's glide-slope row and time-bound box (Sec. 2.2 time
-bounds; the glide-slope bound gamma_gs named in Sec. 5), against their
+bounds; the glide-slope bound gamma_gs named in Sec. 4), against their
 definitions, finite differences and the converged solutions."""
 import math
 

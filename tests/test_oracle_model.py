@@ -1,4 +1,4 @@
-"""Pins of the oracle's model and discretization (Sec. 5, Sec. 2.1-2.3.1)
+"""Pins of the oracle's model and discretization (Sec. 4, Sec. 2.1-2.3.1)
 against closed forms, finite differences and invariants."""
 import math
 
@@ -78,7 +78,7 @@ def test_quaternion_norm_and_mass_monotone(oracle, params):
 
 
 def test_path_constraints_boundaries(oracle, params7):
-    """Each row of g is zero exactly on its bound (Sec. 5; tilt row reading)."""
+    """Each row of g is zero exactly on its bound (Sec. 4; tilt row reading)."""
     p = params7
     x = np.zeros(15)
     x[0] = p["m_dry"]

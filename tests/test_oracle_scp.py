@@ -1,4 +1,4 @@
-"""Pins of the oracle's full SCP solve (Sec. 2.3, Sec. 7): a converged
+"""Pins of the oracle's full SCP solve (Sec. 2.3, Sec. 6): a converged
 trajectory satisfies the nonlinear dynamics on re-propagation, the CTCS
 budget and the path constraints between nodes; replaying recorded counts
 reproduces a solve; the paper's Monte Carlo distribution converges."""
@@ -51,7 +51,7 @@ def test_converged_solution_is_feasible(oracle, inputs, nu, seed):
     - the dynamics: the scaled defect against a 200-substep flow is within the
       solver's own defect tolerance scp_eps_defect (the 10-substep RK4 the
       solver uses differs from the fine flow by far less);
-    - the unit quaternion: the flow preserves ||q|| (Omega(w) is skew, Sec. 5),
+    - the unit quaternion: the flow preserves ||q|| (Omega(w) is skew, Sec. 4),
       so ||q_k|| - 1 can only come from the defects of the nodes before k;
     - the CTCS budget: y_N - y_1 <= (N - 1) eps, and the flow's y agrees with
       a trapezoid sum of s sum_i max(0, g_i)^2 at 41 points per interval (so
@@ -110,12 +110,12 @@ def test_batch_matches_single(oracle, inputs, params):
 def _paper_mc():
     import json
     import os
-    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_sec7_monte_carlo.json")) as fh:
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_sec6_monte_carlo.json")) as fh:
         return json.load(fh)
 
 
 def test_paper_monte_carlo_distribution_converges(oracle, inputs):
-    """Sec. 7 (tests/golden/paper_sec7_monte_carlo.json): r(0) ~ (U(6,9),
+    """Sec. 6 (tests/golden/paper_sec6_monte_carlo.json): r(0) ~ (U(6,9),
     U(3,6), U(1,2)), SCP <= 25, 2500 PIPG iterations: 256 of 256 runs
     converge (on this project's parameter set)."""
     mc = _paper_mc()
