@@ -83,7 +83,9 @@ def parse():
                     help="PIPG layout: 0 autotune cache / automatic, 1 shared memory, 2 registers")
     ap.add_argument("--err-sample", type=int, default=512,
                     help="fp32: instances re-solved in fp64 on the GPU to report the fp32 error (0: off)")
-    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic)")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic, at least 256)")
+    ap.add_argument("--scp-tol-scale", type=float, default=1.0,
+                    help="divide the SCP step and defect tolerances (reading R8) by this factor")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -111,7 +113,21 @@ def workload_name(a):
     soc = "_soc" if getattr(a, "soc", False) else ""
     gs = "_gs" if getattr(a, "glide_slope", False) else ""
     tb = "_tbounds" if (getattr(a, "dt_min", 0) or getattr(a, "dt_max", 0) or getattr(a, "tf_max", 0)) else ""
-    return f"pdg{getattr(a, 'model', '6dof')}_{a.dispersion}_B{a.batch}_{n}{nu}{soc}{gs}{tb}_{a.precision}_{a.mode}"
+    tol = f"_scptol/{a.scp_tol_scale:g}" if getattr(a, "scp_tol_scale", 1.0) != 1.0 else ""
+    return f"pdg{getattr(a, 'model', '6dof')}_{a.dispersion}_B{a.batch}_{n}{nu}{soc}{gs}{tb}{tol}_{a.precision}_{a.mode}"
+
+
+def load_workload_params(a):
+    """Parameters of the workload the flags name (the SCP tolerances divided
+    by --scp-tol-scale)."""
+    from paper_2404_18034_gb300 import inputs
+    p = inputs.load_params(nu=a.nu, model=a.model, soc_thrust=int(getattr(a, "soc", False)),
+                           glide_slope=int(getattr(a, "glide_slope", False)), dt_min=getattr(a, "dt_min", 0.0),
+                           dt_max=getattr(a, "dt_max", 0.0), tf_max=getattr(a, "tf_max", 0.0))
+    k = float(getattr(a, "scp_tol_scale", 1.0))
+    p["scp_eps_step"] = p["scp_eps_step"] / k
+    p["scp_eps_defect"] = p["scp_eps_defect"] / k
+    return p
 
 
 class ClockSampler:
@@ -170,26 +186,45 @@ class ClockSampler:
 
 
 def cpu_oracle_run(p, x0, N, nthreads):
+    """Oracle solves of the rows of x0 (N: one node count, or one per row);
+    returns (converged, wall seconds)."""
     import oracle
     oracle.build()
+    Ns = np.broadcast_to(np.asarray(N, np.int32), (x0.shape[0],)).copy()
     t = time.perf_counter()
-    r = oracle.solve_batch(p, x0, np.full(x0.shape[0], N, np.int32), nthreads=nthreads)
+    r = oracle.solve_batch(p, x0, Ns, nthreads=nthreads)
     dt = time.perf_counter() - t
     return int(np.sum(r["status"] == 0)), dt
 
 
-def cpu_baseline(p, a, seed, sample):
+def cpu_baseline(p, a, seed, sample, budget_s: float = 12.0):
+    """The oracle on the host cores, on a seeded random subsample of the batch
+    (at least 256 instances, else as many as fit in about budget_s), with
+    OpenMP over instances on every core; then the same oracle on one core, on
+    the first 16 instances of that subsample: the per-solve time of a serial
+    CPU solver, the comparison Sec. 6 makes."""
     cores = os.cpu_count() or 1
-    x0 = __import__("paper_2404_18034_gb300.inputs", fromlist=["x"]).dispersion(p, a.batch, seed, a.dispersion)
+    from paper_2404_18034_gb300 import inputs
+    x0 = inputs.dispersion(p, a.batch, seed, a.dispersion)
+    Ns = inputs.node_counts(a.batch, seed) if a.uneven else np.full(a.batch, a.nodes, np.int32)
+    order = np.random.default_rng(seed).permutation(a.batch)
     if sample <= 0:
-        conv, dt = cpu_oracle_run(p, x0[:cores * 2], a.nodes, cores)
-        per = dt / (cores * 2)
-        sample = int(min(a.batch, max(cores * 2, round(15.0 / max(per, 1e-6)))))
-    conv, dt = cpu_oracle_run(p, x0[:sample], a.nodes, cores)
+        probe = order[:cores * 2]
+        conv, dt = cpu_oracle_run(p, x0[probe], Ns[probe], cores)
+        per = dt / len(probe)
+        sample = int(min(a.batch, max(256, round(budget_s / max(per, 1e-6)))))
+    pick = np.sort(order[:sample])
+    conv, dt = cpu_oracle_run(p, x0[pick], Ns[pick], cores)
+    one = pick[:16]
+    conv1, dt1 = cpu_oracle_run(p, x0[one], Ns[one], 1)
     return {"value": conv / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} of the {a.batch} instances of {workload_name(a)} (FP64 oracle, OpenMP over "
-                      f"instances, {cores} threads, {dt:.1f} s); converged solves / wall time",
-            "converged_in_sample": conv}
+            "sample": f"{sample} of the {a.batch} instances of {workload_name(a)}, drawn by a seeded permutation "
+                      f"(FP64 oracle, OpenMP over instances, {cores} threads, {dt:.1f} s); converged solves / wall "
+                      f"time",
+            "converged_in_sample": conv,
+            "single_core": {"value": conv1 / dt1, "unit": "solves/s", "ms_per_solve": 1e3 * dt1 / len(one),
+                            "sample": f"the first {len(one)} instances of that sample on one thread",
+                            "converged_in_sample": conv1}}
 
 
 def run_reference(a):
@@ -197,7 +232,7 @@ def run_reference(a):
     if rank != 0:
         return
     from paper_2404_18034_gb300 import inputs
-    p = inputs.load_params(nu=a.nu, model=a.model)
+    p = load_workload_params(a)
     seed = inputs.config_seed(2)
     x0 = inputs.dispersion(p, a.batch, seed, a.dispersion)
     cores = os.cpu_count() or 1
@@ -375,8 +410,7 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     prec = 0 if a.precision == "fp64" else 1
-    p = inputs.load_params(nu=a.nu, model=a.model, soc_thrust=int(a.soc), glide_slope=int(a.glide_slope),
-                           dt_min=a.dt_min, dt_max=a.dt_max, tf_max=a.tf_max)
+    p = load_workload_params(a)
     seed = shard_seed(inputs.config_seed(2), rank)
     x0h = inputs.dispersion(p, a.batch, seed, a.dispersion)
     x0 = torch.from_numpy(x0h).to(dev)
@@ -484,6 +518,7 @@ def run_ours(a):
                        "nodes": "uniform in {10,15,20,30}" if a.uneven else a.nodes, "model": a.model, "nu": p["nu"],
                        "precision": a.precision, "mode": a.mode,
                        "dispersion": a.dispersion, "parallelism": f"dp{world}",
+                       "scp_eps_step": p["scp_eps_step"], "scp_eps_defect": p["scp_eps_defect"],
                        "l2": "256 MiB buffer written between timed steps",
                        "threads_per_cta": info["threads"], "ctas_per_sm": info["ctas_per_sm"],
                        "pipg_form": {1: "shared-memory blocks", 2: "register-resident blocks"}.get(info["pipg_form"]),

@@ -63,6 +63,7 @@ extern "C" {
 #define PDG_NONFINITE 2   /* a non-finite value appeared */
 #define PDG_BUDGET 3      /* the device-side wall-clock budget ran out */
 #define PDG_BAD_INPUT 4   /* n_nodes out of range or non-finite x0 */
+#define PDG_ABORTED 5     /* stopped by pdg_mc_abort at an SCP iteration boundary */
 
 /* Problem and solver parameters; angles in radians.  Sec. 4 lists the model
  * quantities, Sec. 2.3.2 the scalings P_x, P_u and Sec. 3 the PIPG inputs. */
@@ -118,6 +119,26 @@ void pdg_mc_destroy(pdg_handle* h);
  * error of pdg_mc_init. */
 const char* pdg_mc_last_error(const pdg_handle* h);
 
+/* Abort request (failure handling; no counterpart in the paper).  Sets the
+ * handle's abort word, a word of pinned host memory that pdg_mc_init maps into
+ * the device's address space.  Safe to call from any host thread, also while
+ * a solve of this handle runs on the GPU; it returns at once and waits for
+ * nothing.  Every solve of the handle reads the word at each SCP iteration
+ * boundary (the persistent forms once per CTA before each SCP iteration; the
+ * plain form and the no-allocation entry point once per instance in each SCP
+ * iteration's kernels) and never waits on it: an instance still running stops
+ * there with status PDG_ABORTED, X and U holding its trajectory after the
+ * scp_iters SCP iterations it completed, and instances not yet started stop
+ * before their first iteration (scp_iters 0, X and U the initial guess).
+ * The request stays set, and later solves abort at once, until
+ * pdg_mc_clear_abort.  Gradients of aborted instances are zero.  Returns
+ * PDG_EINVAL for a NULL handle. */
+int pdg_mc_abort(pdg_handle* h);
+
+/* Clear the abort request.  Make sure no solve of the handle is running, or
+ * it may see either value.  Returns PDG_EINVAL for a NULL handle. */
+int pdg_mc_clear_abort(pdg_handle* h);
+
 /* Solve B instances (Sec. 2.3 SCP loop; all of Sec. 2.3.1-3 per iteration).
  *   x0        device [B][NX-1]
  *   n_nodes   device [B] (2..n_max) or NULL for n_max everywhere
@@ -132,7 +153,7 @@ const char* pdg_mc_last_error(const pdg_handle* h);
  *                mode 1 when n_nodes is NULL.
  *   X, U      device outputs (see layouts)
  *   tf, fuel  device [B]: final time sum_k dtau (s_k + s_{k+1})/2 and m_1 - m_N
- *   status    device [B] PDG_CONVERGED ... PDG_BAD_INPUT
+ *   status    device [B] PDG_CONVERGED ... PDG_ABORTED
  *   scp_iters device [B]; pipg_iters device [B] (sum over SCP iterations)
  *   trace     device [B][scp_jmax][2] (power iterations, PIPG iterations per
  *             SCP iteration; zero past the last) or NULL

@@ -35,7 +35,19 @@ struct DParams {
   double s_lo, s_hi; // node box on the dilation: [s_min, s_max] tightened by the time bounds,
   double dt_lo, dt_hi;  // of which dt_min, dt_max scale with N - 1 (0 = off)
   double mp[16];     // constants of a model supplied through PDG_MODEL_HEADER
+  const int* abort_flag;  // the handle's abort word (host memory mapped into the
+                          // device's address space), or null
 };
+
+// The handle's abort request, read at system scope so that a store from a
+// host thread is seen while a kernel runs.  One thread reads; the callers
+// broadcast the answer so that a CTA decides as one.
+__device__ __forceinline__ bool abort_requested(const DParams& P) {
+  if (!P.abort_flag) return false;
+  int v;
+  asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(P.abort_flag) : "memory");
+  return v != 0;
+}
 
 // Per-instance shared-memory layout (element offsets in units of R).  The
 // "image" prefix is what persists between phases (and what the plain form
@@ -66,6 +78,13 @@ struct Lay {
 //   model_init_node<R, NU>(P, x0, t, x, u): initial guess at node fraction t
 // with R in {double, float} and, for the gradient, a dual number type.  The
 // phases use nothing else of the model; P.mp holds its own constants.
+// Optionally (PDG_MODEL_HAS_STM_MASK defined), the structural sparsity of the
+// interval state-transition matrix:
+//   model_stm_row_mask(i)  bit c set unless entry (i, c) of every interval's
+//               A_k is exactly zero for all states, controls and parameters
+//               (the closure of df/dx's pattern under the flow).  The PIPG
+//               products then skip the entries outside the mask; without it
+//               every entry counts.
 #if defined(PDG_MODEL_HEADER)
 #include PDG_MODEL_HEADER
 #elif defined(PDG_MODEL_3DOF)
@@ -82,6 +101,56 @@ static_assert(pdg::IM >= 0 && pdg::IM < pdg::NX - 1, "the cost's mass index must
 static_assert(PDG_MODEL_NU_ALT == 4 || PDG_MODEL_NU_ALT == 7, "controls: nu = 4, optionally nu = 7");
 
 namespace pdg {
+
+#ifndef PDG_MODEL_HAS_STM_MASK
+__host__ __device__ constexpr unsigned model_stm_row_mask(int) { return (1u << NX) - 1u; }
+#endif
+
+// Order in which the PIPG steps visit the entries of hat A^-_k.  A thread of
+// the dual step forms row i of hat A^-_k times a vector, one of the primal
+// step column i; both skip the structural zeros (model_stm_row_mask).  Tasks
+// are sorted by their count of nonzeros, largest first, so that the 32 tasks
+// of a warp need about the same number of FMAs and the warp's first task has
+// the most (the warp runs that many, on the GB300 FP64 pipe each costs a full
+// warp instruction).  A task with fewer entries than its warp's first pads its
+// index list with one of its own structural zeros, which adds exactly nothing.
+struct StmOrder {
+  unsigned char row_order[NXMAX], col_order[NXMAX];  // rows / columns, most nonzeros first
+  unsigned char row_nnz[NXMAX], col_nnz[NXMAX];
+  unsigned long long row_list[NXMAX], col_list[NXMAX];  // 4-bit indices, ascending, then padding
+};
+
+__host__ __device__ constexpr bool stm_nz(int i, int c) { return (model_stm_row_mask(i) >> c) & 1u; }
+
+__host__ __device__ constexpr StmOrder make_stm_order() {
+  StmOrder S{};
+  for (int i = 0; i < NX; ++i) {
+    int nr = 0, nc = 0, zr = -1, zc = -1;
+    unsigned long long lr = 0, lc = 0;
+    for (int c = 0; c < NX; ++c) {
+      if (stm_nz(i, c)) { lr |= (unsigned long long)c << (4 * nr); ++nr; } else if (zc < 0) zc = c;
+      if (stm_nz(c, i)) { lc |= (unsigned long long)c << (4 * nc); ++nc; } else if (zr < 0) zr = c;
+    }
+    for (int j = nr; j < NX; ++j) lr |= (unsigned long long)(zc < 0 ? 0 : zc) << (4 * j);
+    for (int j = nc; j < NX; ++j) lc |= (unsigned long long)(zr < 0 ? 0 : zr) << (4 * j);
+    S.row_nnz[i] = (unsigned char)nr;
+    S.col_nnz[i] = (unsigned char)nc;
+    S.row_list[i] = lr;
+    S.col_list[i] = lc;
+  }
+  for (int a = 0; a < NX; ++a) { S.row_order[a] = (unsigned char)a; S.col_order[a] = (unsigned char)a; }
+  for (int a = 1; a < NX; ++a)  // stable insertion sort, most nonzeros first
+    for (int b = a; b > 0; --b) {
+      if (S.row_nnz[S.row_order[b]] > S.row_nnz[S.row_order[b - 1]]) {
+        const unsigned char t = S.row_order[b]; S.row_order[b] = S.row_order[b - 1]; S.row_order[b - 1] = t;
+      }
+      if (S.col_nnz[S.col_order[b]] > S.col_nnz[S.col_order[b - 1]]) {
+        const unsigned char t = S.col_order[b]; S.col_order[b] = S.col_order[b - 1]; S.col_order[b - 1] = t;
+      }
+    }
+  return S;
+}
+static __constant__ StmOrder kStm = make_stm_order();
 
 // stage buffer of one interval: compact A (SA_A), dense B (NX x nu), then the
 // evaluator's RK4 state of x: base P, accumulator, stage input (NX each)

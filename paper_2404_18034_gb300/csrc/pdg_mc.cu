@@ -170,12 +170,18 @@ k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
     __syncthreads();
     int stat = PDG_MAX_SCP, j;
     for (j = 1; j <= P.scp_jmax; ++j) {
-      if (P.budget_ns > 0.0) {
-        // one clock reading decides for the whole CTA: threads that read the
-        // clock on either side of the limit would part at the next barrier
-        if (threadIdx.x == 0) C.over = double(globaltimer_ns() - C.t_start) > P.budget_ns;
+      if (P.budget_ns > 0.0 || P.abort_flag) {
+        // one clock reading and one read of the abort word decide for the
+        // whole CTA: threads that read either on both sides of a change would
+        // part at the next barrier
+        if (threadIdx.x == 0) {
+          int over = 0;
+          if (P.budget_ns > 0.0 && double(globaltimer_ns() - C.t_start) > P.budget_ns) over = PDG_BUDGET;
+          if (abort_requested(P)) over = PDG_ABORTED;
+          C.over = over;
+        }
         __syncthreads();
-        if (C.over) { stat = PDG_BUDGET; --j; break; }
+        if (C.over) { stat = C.over; --j; break; }
       }
       if (rec) {  // reference and warm start of this SCP iteration (the last one is kept)
         double* rc = rec + (size_t)C.b * rec_stride;
@@ -244,6 +250,18 @@ k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
 // ---------------------------------------------------------------------------
 // plain form: per-instance image in global memory between launches
 // ---------------------------------------------------------------------------
+// The abort request, read once per CTA and broadcast (every thread of the CTA
+// returns the same answer).
+__device__ bool plain_aborted(const DParams& P) {
+  if (!P.abort_flag) return false;
+  __shared__ int ab;
+  if (threadIdx.x == 0) ab = abort_requested(P);
+  __syncthreads();
+  const bool r = ab != 0;
+  __syncthreads();
+  return r;
+}
+
 struct PlainWs {
   void* img;           // [B][istride] of R
   int istride;         // elements of R per instance
@@ -291,6 +309,7 @@ k_plain_disc(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plain
   R* sm = reinterpret_cast<R*>(smraw);
   const int b = blockIdx.x;
   if (W.st[b] != ST_RUNNING) return;
+  if (plain_aborted(P)) return;  // k_plain_update ends the instance
   const int N = Ns ? Ns[b] : Nmax;
   const Lay L = make_lay(N, NU, blockDim.x);
   R* img = reinterpret_cast<R*>(W.img) + (size_t)b * W.istride;
@@ -310,6 +329,7 @@ k_plain_power(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plai
   R* sm = reinterpret_cast<R*>(smraw);
   const int b = blockIdx.x;
   if (W.st[b] != ST_RUNNING) return;
+  if (plain_aborted(P)) return;  // k_plain_update ends the instance
   const int N = Ns ? Ns[b] : Nmax;
   const Lay L = make_lay(N, NU, blockDim.x);
   R* img = reinterpret_cast<R*>(W.img) + (size_t)b * W.istride;
@@ -328,6 +348,7 @@ k_plain_pipg(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plain
   R* sm = reinterpret_cast<R*>(smraw);
   const int b = blockIdx.x;
   if (W.st[b] != ST_RUNNING) return;
+  if (plain_aborted(P)) return;  // k_plain_update ends the instance
   const int N = Ns ? Ns[b] : Nmax;
   const Lay L = make_lay(N, NU, blockDim.x);
   R* img = reinterpret_cast<R*>(W.img) + (size_t)b * W.istride;
@@ -339,7 +360,9 @@ k_plain_pipg(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Plain
   if (threadIdx.x == 0) W.pipg_it[b] = it;
 }
 
-// step_only: the one-iteration API (no status, no outputs).
+// step_only: the one-iteration API (no status, no outputs).  An abort
+// request ends a running instance here, before its step is applied: its
+// outputs are the reference after the SCP iterations it completed.
 template <typename R, int NU>
 __global__ void __launch_bounds__(512, sizeof(R) == 4 ? PDG_FP32_MIN_BLOCKS : 1)
 k_plain_update(const DParams P, int B, int Nmax, const int* __restrict__ Ns, PlainWs W, int step_only,
@@ -355,6 +378,15 @@ k_plain_update(const DParams P, int B, int Nmax, const int* __restrict__ Ns, Pla
   copy_g2s(sm + L.Xb, img + L.Xb, L.Am - L.Xb);      // Xb, Ub
   copy_g2s(sm + L.xh, img + L.xh, L.mup - L.xh);     // xh, uh
   __syncthreads();
+  if (!step_only && plain_aborted(P)) {
+    const int j = W.sit[b];
+    if (trace) {
+      for (int t = threadIdx.x + 2 * j; t < 2 * P.scp_jmax; t += blockDim.x) trace[(size_t)b * P.scp_jmax * 2 + t] = 0;
+    }
+    write_outputs<R, NU>(L, sm, b, Nmax, PDG_ABORTED, j, W.lit[b], X, U, tf, fuel, status, scp_iters, pipg_iters);
+    if (threadIdx.x == 0) { W.st[b] = PDG_ABORTED; atomicAdd(W.done, 1); }
+    return;
+  }
   bool bad;
   const R step = phase_update<R, NU>(P, L, sm, &bad);
   copy_s2g(img + L.Xb, sm + L.Xb, L.Am - L.Xb);
@@ -690,6 +722,12 @@ struct pdg_handle {
   size_t stage_bytes = 0;
   // last launch
   int last_threads = 0, last_ctas = 0, last_smem = 0, last_variant = 0;
+  // abort word: pinned host memory mapped into the device's address space
+  int* abort_host = nullptr;
+  // plain form: the instantiated graph of one SCP iteration, kept between
+  // calls and updated in place when only the kernels' arguments change
+  cudaGraphExec_t plain_exec = nullptr;
+  long long plain_graph_builds = 0, plain_graph_updates = 0;
 };
 
 static std::string g_init_err;
@@ -1001,7 +1039,6 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
   k_plain_init<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, x0, Ns, W, X, U, tf, fuel, status, scp_iters, pipg_iters);
   PDG_CUDA(h, cudaGetLastError());
   cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
   PDG_CUDA(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   k_plain_disc<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W);
   k_plain_power<R, NU><<<B, Tr, smem, s>>>(h->dp, B, h->n_max, Ns, W, nullptr);
@@ -1010,11 +1047,31 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
                                              trace, nullptr);
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   if (ce != cudaSuccess) return fail(h, PDG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-  ce = cudaGraphInstantiate(&exec, graph, 0);
-  if (ce != cudaSuccess) {
-    cudaGraphDestroy(graph);
-    return fail(h, PDG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+  // Capturing is cheap; instantiating is not.  A graph with the same four
+  // kernels (same functions and launch shapes) only changes arguments from
+  // call to call (batch size, buffers), which cudaGraphExecUpdate applies to
+  // the kept executable; anything else instantiates it anew.
+  if (h->plain_exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(h->plain_exec, graph, &info) == cudaSuccess) {
+      ++h->plain_graph_updates;
+    } else {
+      (void)cudaGetLastError();
+      cudaGraphExecDestroy(h->plain_exec);
+      h->plain_exec = nullptr;
+    }
   }
+  if (!h->plain_exec) {
+    ce = cudaGraphInstantiate(&h->plain_exec, graph, 0);
+    if (ce != cudaSuccess) {
+      h->plain_exec = nullptr;
+      cudaGraphDestroy(graph);
+      return fail(h, PDG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    }
+    ++h->plain_graph_builds;
+  }
+  cudaGraphDestroy(graph);
+  cudaGraphExec_t exec = h->plain_exec;
   int rc = 0;
   for (int j = 0; j < h->p.scp_jmax; ++j) {
     ce = cudaGraphLaunch(exec, s);
@@ -1023,8 +1080,6 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
     if (ce != cudaSuccess) { rc = fail(h, PDG_ECUDA, std::string("plain SCP step: ") + cudaGetErrorString(ce)); break; }
     if (*h->pinned_done >= B) break;
   }
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
   if (rc == 0) {
     PDG_CUDA(h, cudaEventRecord(h->ev_out, s));
     PDG_CUDA(h, cudaStreamWaitEvent(us, h->ev_out, 0));
@@ -1268,6 +1323,22 @@ int pdg_mc_init(const pdg_params* p, int n_max, pdg_handle** out) {
   h->threads_override = 0;
   h->device = dev;
   h->num_sms = sms;
+  {
+    void* dptr = nullptr;
+    cudaError_t ea = cudaHostAlloc((void**)&h->abort_host, sizeof(int), cudaHostAllocMapped);
+    if (ea == cudaSuccess) {
+      __atomic_store_n(h->abort_host, 0, __ATOMIC_SEQ_CST);
+      ea = cudaHostGetDevicePointer(&dptr, h->abort_host, 0);
+    }
+    if (ea != cudaSuccess) {
+      if (h->abort_host) cudaFreeHost(h->abort_host);
+  if (h->plain_exec) cudaGraphExecDestroy(h->plain_exec);
+      delete h;
+      g_init_err = std::string("abort word (mapped pinned host memory): ") + cudaGetErrorString(ea);
+      return PDG_ECUDA;
+    }
+    h->dp.abort_flag = static_cast<const int*>(dptr);
+  }
   *out = h;
   g_init_err.clear();
   return PDG_OK;
@@ -1287,6 +1358,8 @@ void pdg_mc_destroy(pdg_handle* h) {
     if (h->cls_events[i]) cudaEventDestroy(h->cls_events[i]);
   }
   if (h->pinned_done) cudaFreeHost(h->pinned_done);
+  if (h->abort_host) cudaFreeHost(h->abort_host);
+  if (h->plain_exec) cudaGraphExecDestroy(h->plain_exec);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
@@ -1294,6 +1367,18 @@ void pdg_mc_destroy(pdg_handle* h) {
 }
 
 const char* pdg_mc_last_error(const pdg_handle* h) { return h ? h->err.c_str() : g_init_err.c_str(); }
+
+int pdg_mc_abort(pdg_handle* h) {
+  if (!h) return PDG_EINVAL;
+  __atomic_store_n(h->abort_host, 1, __ATOMIC_SEQ_CST);
+  return PDG_OK;
+}
+
+int pdg_mc_clear_abort(pdg_handle* h) {
+  if (!h) return PDG_EINVAL;
+  __atomic_store_n(h->abort_host, 0, __ATOMIC_SEQ_CST);
+  return PDG_OK;
+}
 
 int pdg_mc_solve_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes, int mode, double* X, double* U,
                        double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters, int* trace,

@@ -21,6 +21,13 @@ constexpr int SA_A = 12;
 // no RCS torque, so nu = 4 only
 #define PDG_MODEL_NU_ALT 4
 
+// Structural sparsity of the interval STM A_k: the mass depends on no state,
+// r_i on m, r_i, v_i; v_i on m, v_i; y on everything, nothing but y on y.
+#define PDG_MODEL_HAS_STM_MASK 1
+__host__ __device__ constexpr unsigned model_stm_row_mask(int i) {
+  return i == 0 ? 1u : i <= 3 ? (1u | (1u << i) | (1u << (i + 3))) : i <= 6 ? (1u | (1u << i)) : 0xFFu;
+}
+
 // ---------------------------------------------------------------------------
 // One call evaluates, at (x, u): f = s (F, sum |g|_+^2), the nonzero pattern
 // of df/dx in compact form, and df/du densely (8 x NU).

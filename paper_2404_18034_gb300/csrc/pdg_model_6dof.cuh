@@ -15,6 +15,22 @@ constexpr int SA_A = 42;
 #define PDG_MODEL_NU_ALT 7
 #define PDG_MODEL_USES_INERTIA 1
 
+// Structural sparsity of the interval STM A_k (rows i, columns c): the mass
+// depends on no state; r_i on m, r_i, v_i, q, w (through v_i); v_i on m,
+// v_i, q, w; q on q, w; w on w; y on everything, and nothing but y on y.
+// These are the closure of df/dx's pattern (model_jvp) under the flow, for
+// every parameter value (inertia, thrust point, glide slope, nu).
+#define PDG_MODEL_HAS_STM_MASK 1
+__host__ __device__ constexpr unsigned model_stm_row_mask(int i) {
+  constexpr unsigned M = 1u << 0, Q = 0xFu << 7, W = 0x7u << 11;
+  return i == 0 ? M
+       : i <= 3 ? (M | (1u << i) | (1u << (i + 3)) | Q | W)
+       : i <= 6 ? (M | (1u << i) | Q | W)
+       : i <= 10 ? (Q | W)
+       : i <= 13 ? W
+       : 0x7FFFu;
+}
+
 // ---------------------------------------------------------------------------
 // Sec. 4 model.  One call evaluates, at (x, u): f = s (F, sum |g|_+^2), the
 // nonzero pattern of df/dx in compact form, and df/du densely (15 x NU).

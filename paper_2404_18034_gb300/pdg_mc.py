@@ -20,13 +20,13 @@ LIB_PATH = os.environ.get("PDG_MC_LIB", os.path.join(HERE, "libpdg_mc.so"))
 LIB_PATHS = {"6dof": LIB_PATH, "3dof": os.path.join(HERE, "libpdg_mc_3dof.so")}
 NXS = {"6dof": 15, "3dof": 8}
 
-PDG_CONVERGED, PDG_MAX_SCP, PDG_NONFINITE, PDG_BUDGET, PDG_BAD_INPUT = 0, 1, 2, 3, 4
+PDG_CONVERGED, PDG_MAX_SCP, PDG_NONFINITE, PDG_BUDGET, PDG_BAD_INPUT, PDG_ABORTED = 0, 1, 2, 3, 4, 5
 ERRORS = {-1: "PDG_EINVAL", -2: "PDG_ENOMEM", -3: "PDG_ECUDA"}
 EXPORTS = ("pdg_mc_init", "pdg_mc_destroy", "pdg_mc_last_error", "pdg_mc_solve_batch",
            "pdg_mc_solve_batch_host", "pdg_mc_subproblem", "pdg_mc_scp_step", "pdg_mc_launch_info",
            "pdg_mc_set_threads", "pdg_mc_probe_fma", "pdg_mc_solve_batch_noalloc",
            "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form", "pdg_mc_probe_fma_lanes",
-           "pdg_mc_autotune", "pdg_mc_model_nx")
+           "pdg_mc_autotune", "pdg_mc_model_nx", "pdg_mc_abort", "pdg_mc_clear_abort")
 
 
 class PdgParams(C.Structure):
@@ -101,10 +101,12 @@ def load_library(path: Optional[str] = None, model: str = "6dof"):
     L.pdg_mc_autotune.argtypes = [_VP, C.c_int, _VP, _VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_double), _VP]
     L.pdg_mc_pipg_form.argtypes = [_VP]
+    L.pdg_mc_abort.argtypes = [_VP]
+    L.pdg_mc_clear_abort.argtypes = [_VP]
     for name in ("pdg_mc_init", "pdg_mc_solve_batch", "pdg_mc_solve_batch_host", "pdg_mc_subproblem",
                  "pdg_mc_scp_step", "pdg_mc_launch_info", "pdg_mc_set_threads", "pdg_mc_probe_fma",
                  "pdg_mc_solve_batch_noalloc", "pdg_mc_grad_batch", "pdg_mc_set_pipg_form", "pdg_mc_pipg_form",
-                 "pdg_mc_probe_fma_lanes", "pdg_mc_autotune"):
+                 "pdg_mc_probe_fma_lanes", "pdg_mc_autotune", "pdg_mc_abort", "pdg_mc_clear_abort"):
         getattr(L, name).restype = C.c_int
     _libs[(path, model)] = L
     return L
@@ -341,6 +343,15 @@ class Solver:
         self._check(rc, "pdg_mc_autotune")
         self.tuned_threads, self.tuned_form = t.value, f.value
         return t.value, f.value, r.value
+
+    def abort(self):
+        """pdg_mc_abort: ask every running or later solve of this handle to stop
+        at its next SCP iteration boundary (any thread; returns at once)."""
+        self._check(self.lib.pdg_mc_abort(self.h), "pdg_mc_abort")
+
+    def clear_abort(self):
+        """pdg_mc_clear_abort."""
+        self._check(self.lib.pdg_mc_clear_abort(self.h), "pdg_mc_clear_abort")
 
     def set_pipg_form(self, form: int):
         """0 automatic, 1 blocks in shared memory, 2 blocks in registers."""
