@@ -465,8 +465,9 @@ def run_ours(a):
     value = conv_all / (total_ms_max * 1e-3)
 
     # roofline of the dominant kernel (the persistent solve kernel is the whole step)
-    fl = flops.solve_flops(Ns_h if a.uneven else np.full(a.batch, a.nodes), p["nu"], p["rk4_substeps"], scp, pow_it,
-                           pipg, a.model)
+    Nv = Ns_h if a.uneven else np.full(a.batch, a.nodes)
+    fl = flops.solve_flops(Nv, p["nu"], p["rk4_substeps"], scp, pow_it, pipg, a.model)
+    fl_dense = flops.solve_flops(Nv, p["nu"], p["rk4_substeps"], scp, pow_it, pipg, a.model, dense=True)
     launch_s = float(np.mean(ms)) * 1e-3
     achieved = fl / launch_s / 1e12
     clocks = clk.summary()
@@ -535,6 +536,9 @@ def run_ours(a):
                                                           + a.batch * 28),
                          "kernel": "whole plain-form step" if mode == 0 else "k_persistent",
                          "flops_per_launch": fl,
+                         "flops_count": "structural nonzeros of hat A^- only (flops.py); frac_dense_count counts "
+                                        "every entry, as a solver multiplying the zeros would",
+                         "frac_dense_count": fl_dense / launch_s / 1e12 / peak_nominal,
                          "peak_source": f"derived: {SMS} SMs x {FMA_PER_CLK[a.precision]} "
                                         f"{a.precision.upper()} FMA/clk x 2 flop x {MAX_SM_MHZ:.0f} MHz",
                          "probe_tflops": probe,

@@ -118,7 +118,9 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
   for (int t = tid; t < PX + PU; t += T) {
     if (t < PX) {
       if (t < nxk) {
-        const int k = t / NX + 1, i = t - NX * (k - 1), o = k * NX + i;
+        // columns in kStm.col_order, structural zeros skipped (as in phase_pipg)
+        const int cr = t / (N - 1);
+        const int k = t - cr * (N - 1) + 1, i = kStm.col_order[cr], o = k * NX + i;
         const bool last = k == N - 1;
         const int km = last ? 0 : k;
         const double xv = xt[o];
@@ -127,7 +129,12 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
         double Gc = G0;
         const double* a = Am + km * NX * NX + i;
         const double* f = vph + km * NX;
-        for (int r = 0; r < NX; ++r) Gc = fma(a[r * NX], f[r], Gc);
+        const int nj = kStm.col_nnz[kStm.col_order[(t & ~31) / (N - 1)]];
+        const unsigned long long lst = kStm.col_list[i];
+        for (int j = 0; j < nj; ++j) {
+          const int r = int(lst >> (4 * j)) & 15;
+          Gc = fma(a[r * NX], f[r], Gc);
+        }
         const double G = last ? G0 : Gc;
         const double cost = (last && i == IM) ? acost : 0.0;
         double xn = fma(-alpha, G, fma(c1, xv, cost));
@@ -179,24 +186,31 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
   for (int t = tid; t < PM + 32; t += T) {
     if (t < PM) {
       if (t < nm) {
-        const int k = t / NX, i = t - NX * k;
-        const double f = vph[t], a = nup[t], b = num[t];
+        // rows in kStm.row_order, structural zeros skipped
+        const int rr = t / (N - 1);
+        const int k = t - rr * (N - 1), i = kStm.row_order[rr], o = k * NX + i;
+        const double f = vph[o], a = nup[o], b = num[o];
         const double pa = a - alpha * (wep + f), pb = b - alpha * (wep - f);
         const bool ma = pa > 0, mb = pb > 0;
         const double mp = ma ? pa : 0.0, mm = mb ? pb : 0.0;
-        sm[A.mup_m + t] = ma ? 1.0 : 0.0;
-        sm[A.mum_m + t] = mb ? 1.0 : 0.0;
-        double r = sm[L.w + t] + (fma(2.0, mp, -a) - fma(2.0, mm, -b)) - dx[(k + 1) * NX + i];
-        for (int c = 0; c < NX; ++c) r = fma(Am[(k * NX + i) * NX + c], dx[k * NX + c], r);
+        sm[A.mup_m + o] = ma ? 1.0 : 0.0;
+        sm[A.mum_m + o] = mb ? 1.0 : 0.0;
+        double r = sm[L.w + o] + (fma(2.0, mp, -a) - fma(2.0, mm, -b)) - dx[(k + 1) * NX + i];
+        const int nj = kStm.row_nnz[kStm.row_order[(t & ~31) / (N - 1)]];
+        const unsigned long long lst = kStm.row_list[i];
+        for (int j = 0; j < nj; ++j) {
+          const int c = int(lst >> (4 * j)) & 15;
+          r = fma(Am[o * NX + c], dx[k * NX + c], r);
+        }
         for (int c = 0; c < NU; ++c)
-          r = fma(Bp[(k * NX + i) * NU + c], du[(k + 1) * NU + c], fma(Bm[(k * NX + i) * NU + c], du[k * NU + c], r));
-        sm[L.mup + t] = mp;
-        sm[L.mum + t] = mm;
-        sm[L.phi + t] = fma(beta, r, f);
+          r = fma(Bp[o * NU + c], du[(k + 1) * NU + c], fma(Bm[o * NU + c], du[k * NU + c], r));
+        sm[L.mup + o] = mp;
+        sm[L.mum + o] = mm;
+        sm[L.phi + o] = fma(beta, r, f);
         if (update) {
-          nup[t] = a + rho * (mp - a);
-          num[t] = b + rho * (mm - b);
-          vph[t] = f + rho * beta * r;
+          nup[o] = a + rho * (mp - a);
+          num[o] = b + rho * (mm - b);
+          vph[o] = f + rho * beta * r;
         }
       }
     } else {
@@ -288,21 +302,28 @@ __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& 
   for (int t = tid; t < PX + round32(nuu); t += T) {
     if (t < PX) {
       if (t < nx) {
-        const int k = t / NX, i = t - NX * k;
+        // columns in kStm.col_order (N nodes each), structural zeros skipped
+        const int cr = t / N;
+        const int k = t - cr * N, i = kStm.col_order[cr], o = k * NX + i;
         const bool hasA = k < N - 1, hasP = k > 0;
         const int ka = hasA ? k : 0, kp = hasP ? k - 1 : 0;
         double dA = 0;
         const double* a = Am + ka * NX * NX + i;
         const double* f = rb + ka * NX;
-        for (int r = 0; r < NX; ++r) dA = fma(a[r * NX], f[r], dA);
+        const int nj = kStm.col_nnz[kStm.col_order[(t & ~31) / N]];
+        const unsigned long long lst = kStm.col_list[i];
+        for (int j = 0; j < nj; ++j) {
+          const int r = int(lst >> (4 * j)) & 15;
+          dA = fma(a[r * NX], f[r], dA);
+        }
         const double hd = (hasP ? hb[kp] : 0.0) - (hasA ? hb[ka] : 0.0);
         double d = fma(i == IY ? 1.0 : 0.0, hd, hasA ? dA : 0.0);
         d -= hasP ? rb[kp * NX + i] : 0.0;
-        const double xhb = fma(2.0, d, fma(rho, xtb[t], last ? sm[A.xob + t] : 0.0));
+        const double xhb = fma(2.0, d, fma(rho, xtb[o], last ? sm[A.xob + o] : 0.0));
         const bool fixed = (k == 0) || (k == N - 1 && P.fix_f[i]);
         const double nf = fixed ? 0.0 : 1.0;
-        xtb[t] = fma(nf * c1, xhb, fma(omr, xtb[t], -d));
-        Gb[t] = (-alpha * nf) * xhb;
+        xtb[o] = fma(nf * c1, xhb, fma(omr, xtb[o], -d));
+        Gb[o] = (-alpha * nf) * xhb;
       }
     } else {
       const int q = t - PX;
@@ -330,21 +351,28 @@ __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& 
   for (int t = tid; t < PM + 32; t += T) {
     if (t < PM) {
       if (t < nm) {
-        const int k = t / NX, i = t - NX * k;
+        // rows in kStm.row_order, structural zeros skipped
+        const int rr = t / (N - 1);
+        const int k = t - rr * (N - 1), i = kStm.row_order[rr], o = k * NX + i;
         const int kk = k >= 1 ? k : 0;
-        double fb = vphb[t];
+        double fb = vphb[o];
         double fa = fb;
-        for (int c = 0; c < NX; ++c) fa = fma(Am[(kk * NX + i) * NX + c], Gb[kk * NX + c], fa);
+        const int nj = kStm.row_nnz[kStm.row_order[(t & ~31) / (N - 1)]];
+        const unsigned long long lst = kStm.row_list[i];
+        for (int j = 0; j < nj; ++j) {
+          const int c = int(lst >> (4 * j)) & 15;
+          fa = fma(Am[(kk * NX + i) * NX + c], Gb[kk * NX + c], fa);
+        }
         fb = k >= 1 ? fa : fb;
         fb -= Gb[(k + 1) * NX + i];
         for (int c = 0; c < NU; ++c)
-          fb = fma(Bp[(k * NX + i) * NU + c], Gub[(k + 1) * NU + c], fma(Bm[(k * NX + i) * NU + c], Gub[k * NU + c], fb));
-        vphb[t] = fb;
-        if (t < NX) {
-          const double ph = vph[t];
+          fb = fma(Bp[o * NU + c], Gub[(k + 1) * NU + c], fma(Bm[o * NU + c], Gub[k * NU + c], fb));
+        vphb[o] = fb;
+        if (k == 0) {  // interval 1: cotangents of hat B^-_1, hat B^+_1 (row i)
+          const double ph = vph[o];
           for (int c = 0; c < NU; ++c) {
-            sm[A.cBm + t * NU + c] = fma(ph, Gub[c], sm[A.cBm + t * NU + c]);
-            sm[A.cBp + t * NU + c] = fma(ph, Gub[NU + c], sm[A.cBp + t * NU + c]);
+            sm[A.cBm + i * NU + c] = fma(ph, Gub[c], sm[A.cBm + i * NU + c]);
+            sm[A.cBp + i * NU + c] = fma(ph, Gub[NU + c], sm[A.cBp + i * NU + c]);
           }
         }
       }

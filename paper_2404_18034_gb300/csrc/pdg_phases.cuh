@@ -224,17 +224,25 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
     for (int t = tid; t < PM + 32; t += T) {
       if (t < PM) {
         if (t < nm) {
-          const int k = t / NX, i = t - NX * k;
+          // rows in kStm.row_order, structural zeros skipped (as in PIPG)
+          const int rr = t / (N - 1);
+          const int k = t - rr * (N - 1), i = kStm.row_order[rr];
+          const int o = k * NX + i;
           const R* a = Am + (k * NX + i) * NX;
           const R* xk = px + k * NX;
-          R r = pp[t] - pn[t] - px[(k + 1) * NX + i];
-#pragma unroll
-          for (int cc = 0; cc < NX; ++cc) r += a[cc] * xk[cc];
+          R r = pp[o] - pn[o] - px[(k + 1) * NX + i];
+          const int nj = kStm.row_nnz[kStm.row_order[(t & ~31) / (N - 1)]];
+          const unsigned long long lst = kStm.row_list[i];
+#pragma unroll 5
+          for (int j = 0; j < nj; ++j) {
+            const int cc = int(lst >> (4 * j)) & 15;
+            r += a[cc] * xk[cc];
+          }
           const R* bm = Bm + (k * NX + i) * NU;
           const R* bp = Bp + (k * NX + i) * NU;
 #pragma unroll
           for (int cc = 0; cc < NU; ++cc) r += bm[cc] * pu[k * NU + cc] + bp[cc] * pu[(k + 1) * NU + cc];
-          ph[t] = r * isig;
+          ph[o] = r * isig;
         }
       } else {
         const int k = t - PM;
@@ -249,20 +257,27 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
         if (t < nx) {
           // branch-free, as the PIPG x step: blocks that do not exist (the
           // last node's A, the first node's coupling) run on valid data and
-          // selects discard them; the CTCS terms ride on a 0/1-weighted FMA
-          const int k = t / NX, i = t - NX * k;
+          // selects discard them; the CTCS terms ride on a 0/1-weighted FMA.
+          // Columns in kStm.col_order (N nodes each), structural zeros skipped.
+          const int cr = t / N;
+          const int k = t - cr * N, i = kStm.col_order[cr];
           const bool hasA = k < N - 1, hasP = k > 0;
           const int ka = hasA ? k : 0, kp = hasP ? k - 1 : 0;
           R gc = 0;
           const R* a = Am + ka * NX * NX + i;
           const R* f = ph + ka * NX;
-#pragma unroll
-          for (int r = 0; r < NX; ++r) gc = fma(a[r * NX], f[r], gc);
+          const int nj = kStm.col_nnz[kStm.col_order[(t & ~31) / N]];
+          const unsigned long long lst = kStm.col_list[i];
+#pragma unroll 5
+          for (int j = 0; j < nj; ++j) {
+            const int r = int(lst >> (4 * j)) & 15;
+            gc = fma(a[r * NX], f[r], gc);
+          }
           R g = hasA ? gc : R(0);
           const R dth = (hasP ? pt[kp] : R(0)) - (hasA ? pt[ka] : R(0));
           g = fma(i == IY ? R(1) : R(0), dth, g);
           g -= hasP ? ph[kp * NX + i] : R(0);
-          px[t] = g;
+          px[k * NX + i] = g;
           s2 += g * g;
         }
       } else if (t < PX + PU) {
@@ -398,8 +413,12 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
       if (t < PX) {
         if (t < nxk) {
           // branch-free: on GB300 a divergent FP64 instruction costs a full
-          // warp slot, and per-component special cases split the warp
-          const int k = t / NX + 1, i = t - NX * (k - 1);
+          // warp slot, and per-component special cases split the warp.
+          // Tasks run column by column in kStm.col_order (N - 1 nodes each),
+          // so a warp's columns have about as many structural nonzeros as
+          // its first task's, which bounds its FMA count.
+          const int cr = t / (N - 1);
+          const int k = t - cr * (N - 1) + 1, i = kStm.col_order[cr];
           const int o = k * NX + i;
           const bool last = k == N - 1;
           const int km = last ? 0 : k;  // the last node has no A block: any valid one, result discarded
@@ -408,8 +427,13 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
           R Gc = G0;
           const R* a = Am + km * NX * NX + i;
           const R* f = vph + km * NX;
-#pragma unroll
-          for (int r = 0; r < NX; ++r) Gc = fma(a[r * NX], f[r], Gc);
+          const int nj = kStm.col_nnz[kStm.col_order[(t & ~31) / (N - 1)]];
+          const unsigned long long lst = kStm.col_list[i];
+#pragma unroll 5
+          for (int j = 0; j < nj; ++j) {
+            const int r = int(lst >> (4 * j)) & 15;
+            Gc = fma(a[r * NX], f[r], Gc);
+          }
           const R G = last ? G0 : Gc;
           // e_cost = -e_m on x_N (maximize m_N) folded into the same FMA
           const R cost = (last && i == IM) ? alpha * wcost : R(0);
@@ -506,36 +530,44 @@ __device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int fo
     for (int t = tid; t < PM + 32; t += T) {
       if (t < PM) {
         if (t < nm) {
-          const int k = t / NX, i = t - NX * k;
-          const R f = vph[t], a = nup[t], b = num[t];
+          // rows in kStm.row_order, N - 1 intervals each (see the x step)
+          const int rr = t / (N - 1);
+          const int k = t - rr * (N - 1), i = kStm.row_order[rr];
+          const int o = k * NX + i;
+          const R f = vph[o], a = nup[o], b = num[o];
           const R mp = max0(a - alpha * f);
           const R mm = max0(b + alpha * f);
-          nup[t] = omr * a + (rho * mp - raw);
-          num[t] = omr * b + (rho * mm - raw);
+          nup[o] = omr * a + (rho * mp - raw);
+          num[o] = omr * b + (rho * mm - raw);
           if constexpr (chk) {
-            const R op = mup[t], om = mum[t];
+            const R op = mup[o], om = mum[o];
             zn = umax(zn, umax(OB::nonneg(mp), OB::nonneg(mm)));
             zo = umax(zo, umax(OB::nonneg(op), OB::nonneg(om)));
             zd = umax(zd, umax(OB::abs(mp - op), OB::abs(mm - om)));
           }
-          mup[t] = mp;
-          mum[t] = mm;
+          mup[o] = mp;
+          mum[o] = mm;
           const R* a_ = Am + (k * NX + i) * NX;
           const R* d = dx + k * NX;
-          R r = wv[t] + (fma(R(2), mp, -a) - fma(R(2), mm, -b)) - dx[(k + 1) * NX + i];
-#pragma unroll
-          for (int cc = 0; cc < NX; ++cc) r += a_[cc] * d[cc];
+          R r = wv[o] + (fma(R(2), mp, -a) - fma(R(2), mm, -b)) - dx[(k + 1) * NX + i];
+          const int nj = kStm.row_nnz[kStm.row_order[(t & ~31) / (N - 1)]];
+          const unsigned long long lst = kStm.row_list[i];
+#pragma unroll 5
+          for (int j = 0; j < nj; ++j) {
+            const int cc = int(lst >> (4 * j)) & 15;
+            r += a_[cc] * d[cc];
+          }
           const R* bm = Bm + (k * NX + i) * NU;
           const R* bp = Bp + (k * NX + i) * NU;
 #pragma unroll
           for (int cc = 0; cc < NU; ++cc) { r += bm[cc] * du[k * NU + cc]; r += bp[cc] * du[(k + 1) * NU + cc]; }
           const R pn = f + beta * r;
-          vph[t] = f + rb * r;  // = f + rho (pn - f)
+          vph[o] = f + rb * r;  // = f + rho (pn - f)
           if constexpr (chk) {
-            const R old = phi[t];
+            const R old = phi[o];
             rn = umax(rn, OB::abs(pn)); ro = umax(ro, OB::abs(old)); rd = umax(rd, OB::abs(pn - old));
           }
-          phi[t] = pn;
+          phi[o] = pn;
         }
       } else {
         // CTCS rows, one warp (N - 1 <= 31 lanes used; all lanes shuffle)

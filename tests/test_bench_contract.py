@@ -33,12 +33,14 @@ def test_algorithmic_flop_counts():
     """The per-iteration and per-discretization figures the roofline uses
     (one FMA = 2 flops) at N = 15, nu = 4."""
     from paper_2404_18034_gb300 import flops
-    # 6-DoF: 4 (N-1)(225 + 30 nu) block-product flops plus the vector work
-    assert flops.pipg_iter(15, 4) == 4 * 14 * (225 + 120) + 9 * 19 * 15 + 9 * 2 * 15 * 14 + 8 * 16 * 14
-    assert flops.pipg_iter(15, 4) == 27457
+    # 6-DoF: 4 (N-1)(110 + 30 nu) block-product flops (110 structural nonzeros
+    # of hat A^-) plus the vector work; dense: 225 entries
+    assert flops.pipg_iter(15, 4) == 4 * 14 * (110 + 120) + 9 * 19 * 15 + 9 * 2 * 15 * 14 + 8 * 16 * 14
+    assert flops.pipg_iter(15, 4, dense=True) == 4 * 14 * (225 + 120) + 9 * 19 * 15 + 9 * 2 * 15 * 14 + 8 * 16 * 14
+    assert flops.pipg_iter(15, 4, dense=True) == 27457
     assert abs(flops.discretization(15, 4, 10) - 2.45e6) < 0.01e6
     # 3-DoF: the same formulas with NX = 8
-    assert flops.pipg_iter(15, 4, "3dof") == 4 * 14 * (64 + 64) + 9 * 12 * 15 + 9 * 2 * 8 * 14 + 8 * 9 * 14
+    assert flops.pipg_iter(15, 4, "3dof") == 4 * 14 * (24 + 64) + 9 * 12 * 15 + 9 * 2 * 8 * 14 + 8 * 9 * 14
     assert flops.discretization(2, 4, 10, "3dof") == 10 * 4 * (16 * (2 * 13 + 24) + 2 * 4 * 2 * 8 + 100)
     # a solve's flops are the sums over its executed counters
     assert flops.solve_flops([15], 4, 10, [2], [3], [5]) == \

@@ -65,6 +65,8 @@ def test_declared_stm_sparsity_matches_oracle(tmp_path, oracle, inputs, model, d
     seen = _sampled_pattern(oracle, inputs, model, nx)
     assert not np.any(seen & ~mask), np.argwhere(seen & ~mask)   # nothing nonzero outside the mask
     np.testing.assert_array_equal(seen, mask)                     # and the mask is no looser than needed
+    from paper_2404_18034_gb300 import flops
+    assert flops.MODELS[model][3] == int(mask.sum())              # the roofline's count of hat A^- nonzeros
     # the visiting order: rows and columns by nonzero count, largest first;
     # index lists hold exactly the nonzeros, then a structural zero
     rows = [o[0] for o in order]
