@@ -53,7 +53,9 @@ struct AdjLay {
   int Sb, rb, hb, Gb, Gub, mup_m, mum_m, th_m, u_m, Xo, Uo, xob, uob, cA, cBm, cBp, cw, gacc, td, tang, total;
 };
 
-__host__ __device__ inline AdjLay make_adj(const Lay& L, int nu, int threads) {
+// tangent = false: without the tangent discretization's region (the adjoint
+// kernel leaves that part to a kernel of its own).
+__host__ __device__ inline AdjLay make_adj(const Lay& L, int nu, int threads, bool tangent = true) {
   AdjLay A;
   const int N = L.N;
   A.ss = L.dx - L.xt;
@@ -83,10 +85,16 @@ __host__ __device__ inline AdjLay make_adj(const Lay& L, int nu, int threads) {
   // tangent discretization: per group a Dual stage buffer and the evaluator's x state
   const int per = NX + 2 * nu + 1;
   const int groups = threads / per;
-  A.tang = o; o += groups * 2 * (SA_A + NX * nu + 3 * NX);
+  A.tang = o; o += tangent ? groups * 2 * (SA_A + NX * nu + 3 * NX) : 0;
   A.total = o;
   return A;
 }
+
+// What the tangent kernel needs of an instance, written by the adjoint kernel
+// (doubles): the first node of the reference, its first two control nodes,
+// the unscaled cotangents of hat A^-_1, hat B^-_1, hat B^+_1, hat w_1, and the
+// gradient accumulated so far.
+__host__ __device__ constexpr int tangent_rec_size(int nu) { return NX + 2 * nu + NX * NX + 2 * NX * nu + NX + 16; }
 
 // One PIPG_custom iteration on the state (xt .. vth) in shared memory, with no
 // stop test, recording the projection masks; with update = false the state is

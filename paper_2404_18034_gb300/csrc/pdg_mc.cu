@@ -41,9 +41,17 @@ using namespace pdg;
 // per dual row plus the control lanes, so its kernels are built for up to
 // PDG_REG_MAXT threads (FP32) or 512 (FP64).
 #define PDG_REG_MAXT_F32 576
+// FP64 solve kernels: compiled for up to PDG_FP64_MAXT threads with at least
+// PDG_FP64_MINB CTAs per SM (the register budget is 65536 / (threads x CTAs))
+#ifndef PDG_FP64_MAXT
+#define PDG_FP64_MAXT 512
+#endif
+#ifndef PDG_FP64_MINB
+#define PDG_FP64_MINB 1
+#endif
 #define PDG_LB(R, PV)                                                                       \
-  __launch_bounds__((PV) == 2 && sizeof(R) == 4 ? PDG_REG_MAXT_F32 : 512,                   \
-                    sizeof(R) == 4 && (PV) != 2 ? PDG_FP32_MIN_BLOCKS : 1)
+  __launch_bounds__((PV) == 2 && sizeof(R) == 4 ? PDG_REG_MAXT_F32 : (sizeof(R) == 8 ? PDG_FP64_MAXT : 512), \
+                    sizeof(R) == 4 && (PV) != 2 ? PDG_FP32_MIN_BLOCKS : (sizeof(R) == 8 ? PDG_FP64_MINB : 1))
 
 namespace {
 
@@ -485,19 +493,23 @@ __global__ void k_pack(int B, int Nmax, int threads, const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // gradient of the last SCP iteration (see pdg_adjoint.cuh), FP64
 // ---------------------------------------------------------------------------
+// k_grad runs everything but the forward-mode discretization of the first
+// interval, whose dual-number arithmetic needs far more registers than the
+// reverse PIPG loop: that part runs in k_grad_tangent, after it, so that the
+// reverse loop keeps two CTAs per SM.  tg receives the record
+// k_grad_tangent starts from (tangent_rec_size doubles per instance).
 template <int NU>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 2)
 k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
        const double* __restrict__ rec, int rec_stride, const int* __restrict__ status,
        const double* __restrict__ gf_in, const double* __restrict__ gt_in, double* ck, long long ck_stride,
-       int nck_max, int ckrec, double* grad, double* fuel_out, double* touch_out) {
+       int nck_max, int ckrec, double* tg, double* fuel_out, double* touch_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double* sm = reinterpret_cast<double*>(smraw);
   const int b = blockIdx.x;
   const int N = Ns ? Ns[b] : Nmax;
   const int st = status[b];
   if (N < 2 || N > Nmax || !(st == PDG_CONVERGED || st == PDG_MAX_SCP)) {
-    if (threadIdx.x < NX - 1) grad[(size_t)b * (NX - 1) + threadIdx.x] = 0.0;
     if (threadIdx.x == 0) {
       if (fuel_out) fuel_out[b] = 0.0;
       if (touch_out) touch_out[b] = 0.0;
@@ -505,7 +517,7 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
     return;
   }
   const Lay L = make_lay(N, NU, blockDim.x);
-  const AdjLay AL = make_adj(L, NU, blockDim.x);
+  const AdjLay AL = make_adj(L, NU, blockDim.x, false);
   const double gf = gf_in ? gf_in[b] : 0.0, gt = gt_in ? gt_in[b] : 0.0;
   const double* rc = rec + (size_t)b * rec_stride;
   const int ow = N * (NX + NU), nw = L.img - L.xh;
@@ -629,9 +641,49 @@ k_grad(const DParams P, int B, int Nmax, const double* __restrict__ x0, const in
     sm[AL.cw + i] *= P.Pxinv[i];
   }
   __syncthreads();
-  tangent_first_interval<NU>(P, L, AL, sm);
+  // the tangent kernel's record: x_bar_1, u_bar_1, u_bar_2, then cA .. gacc
+  // (contiguous in the layout)
+  double* r = tg + (size_t)b * tangent_rec_size(NU);
+  for (int t = threadIdx.x; t < tangent_rec_size(NU); t += blockDim.x)
+    r[t] = t < NX ? sm[L.Xb + t] : t < NX + 2 * NU ? sm[L.Ub + t - NX] : sm[AL.cA + t - NX - 2 * NU];
+}
+
+// The forward-mode part of the gradient: the first interval's RK4
+// discretization in dual arithmetic along every direction of x0, its
+// sensitivities contracted with the block cotangents k_grad recorded, added
+// to the gradient k_grad accumulated (see tangent_first_interval).
+template <int NU>
+__global__ void __launch_bounds__(256, 1)
+k_grad_tangent(const DParams P, int B, int Nmax, const int* __restrict__ Ns, const int* __restrict__ status,
+               const double* __restrict__ tg, double* grad) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sm = reinterpret_cast<double*>(smraw);
+  const int b = blockIdx.x;
+  const int N = Ns ? Ns[b] : Nmax;
+  const int st = status[b];
+  if (N < 2 || N > Nmax || !(st == PDG_CONVERGED || st == PDG_MAX_SCP)) {
+    if (threadIdx.x < NX - 1) grad[(size_t)b * (NX - 1) + threadIdx.x] = 0.0;
+    return;
+  }
+  // a layout holding only what tangent_first_interval reads: the record, then
+  // the dual-number stage buffers
+  Lay L{};
+  L.N = N;
+  L.Xb = 0;
+  L.Ub = NX;
+  AdjLay A{};
+  A.cA = NX + 2 * NU;
+  A.cBm = A.cA + NX * NX;
+  A.cBp = A.cBm + NX * NU;
+  A.cw = A.cBp + NX * NU;
+  A.gacc = A.cw + NX;
+  A.tang = (A.gacc + 16 + 1) & ~1;
+  const double* r = tg + (size_t)b * tangent_rec_size(NU);
+  for (int t = threadIdx.x; t < tangent_rec_size(NU); t += blockDim.x) sm[t] = r[t];
   __syncthreads();
-  if (threadIdx.x < NX - 1) grad[(size_t)b * (NX - 1) + threadIdx.x] = sm[AL.gacc + threadIdx.x];
+  tangent_first_interval<NU>(P, L, A, sm);
+  __syncthreads();
+  if (threadIdx.x < NX - 1) grad[(size_t)b * (NX - 1) + threadIdx.x] = sm[A.gacc + threadIdx.x];
 }
 
 
@@ -1241,8 +1293,14 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
                     double* grad, double* fuel_out, double* touch_out, int* status_out, cudaStream_t s) {
   const int Tg = 256;
   const Lay Lg = make_lay(h->n_max, NU, Tg);
-  const AdjLay Ag = make_adj(Lg, NU, Tg);
+  const AdjLay Ag = make_adj(Lg, NU, Tg, false);
   const size_t smem_g = (size_t)Ag.total * sizeof(double);
+  // the tangent kernel: as many groups of one evaluator and NX + 2 nu columns
+  // as fit in 256 threads, and their dual-number stage buffers after the record
+  constexpr int PER = NX + 2 * NU + 1;
+  const int Tt = (256 / PER) * PER;
+  const int tang_off = (tangent_rec_size(NU) + 1) & ~1;
+  const size_t smem_t = sizeof(double) * ((size_t)tang_off + 2 * (size_t)(256 / PER) * (SA_A + NX * NU + 3 * NX));
   if (smem_g > 232448) return fail(h, PDG_EINVAL, "gradient kernel does not fit in shared memory for this n_max");
   if (h->p.rk4_substeps > 32) return fail(h, PDG_EINVAL, "gradients support at most 32 RK4 substeps");
   const int ss = Ag.ss;
@@ -1262,7 +1320,8 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
   const size_t bX = sizeof(double) * (size_t)B * h->n_max * NX, bU = sizeof(double) * (size_t)B * h->n_max * NU;
   const size_t bB = sizeof(double) * B, bI = sizeof(int) * B, bL = sizeof(long long) * B;
   const size_t bR = sizeof(double) * (size_t)B * rec_stride, bC = sizeof(double) * (size_t)B * ck_stride;
-  const size_t need = al(bX) + al(bU) + 2 * al(bB) + 2 * al(bI) + al(bL) + al(bR) + al(bC);
+  const size_t bT = sizeof(double) * (size_t)B * tangent_rec_size(NU);
+  const size_t need = al(bX) + al(bU) + 2 * al(bB) + 2 * al(bI) + al(bL) + al(bR) + al(bC) + al(bT);
   if (h->gws_bytes < need) {
     if (h->gws) cudaFree(h->gws);
     h->gws = nullptr;
@@ -1279,6 +1338,7 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
   int* sc = (int*)c; c += al(bI);
   long long* pi = (long long*)c; c += al(bL);
   double* rec = (double*)c; c += al(bR);
+  double* tgr = (double*)c; c += al(bT);
   double* ck = (double*)c;
   h->rec_ptr = rec;
   h->rec_stride = rec_stride;
@@ -1290,7 +1350,10 @@ static int run_grad(pdg_handle* h, int B, const double* x0, const int* Ns, const
   if (rc) return rc;
   PDG_CUDA(h, cudaFuncSetAttribute(k_grad<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g));
   k_grad<NU><<<B, Tg, smem_g, s>>>(h->dp, B, h->n_max, x0, Ns, rec, rec_stride, st, gf, gt, ck, ck_stride, nck_max,
-                                   ckrec ? 1 : 0, grad, fuel_out, touch_out);
+                                   ckrec ? 1 : 0, tgr, fuel_out, touch_out);
+  PDG_CUDA(h, cudaGetLastError());
+  PDG_CUDA(h, cudaFuncSetAttribute(k_grad_tangent<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
+  k_grad_tangent<NU><<<B, Tt, smem_t, s>>>(h->dp, B, h->n_max, Ns, st, tgr, grad);
   PDG_CUDA(h, cudaGetLastError());
   if (status_out) PDG_CUDA(h, cudaMemcpyAsync(status_out, st, sizeof(int) * B, cudaMemcpyDeviceToDevice, s));
   return 0;

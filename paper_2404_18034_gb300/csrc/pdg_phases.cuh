@@ -342,8 +342,13 @@ template <bool B> struct ChkTag { static constexpr bool value = B; };
 // CK (gradient solves only): before iterations 1, 51, 101, ... the state
 // (x~, u~, nu~+-, phi~, theta~; nu~ unshifted) is copied to ck, one record of
 // L.dx - L.xt values per 50 iterations, for the adjoint's recomputation.
+#ifdef PDG_PIPG_NOINLINE
+#define PDG_PIPG_ATTR __noinline__
+#else
+#define PDG_PIPG_ATTR
+#endif
 template <typename R, int NU, bool CK = false>
-__device__ int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force, double* ck = nullptr) {
+__device__ PDG_PIPG_ATTR int phase_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force, double* ck = nullptr) {
   using OB = OrdBits<R>;
   using U = typename OB::U;
   const int N = L.N, T = blockDim.x, tid = threadIdx.x;
