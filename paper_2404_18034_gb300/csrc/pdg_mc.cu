@@ -21,6 +21,8 @@
 #include <mutex>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pdg_mc.h"
 #include "pdg_adjoint.cuh"
 
@@ -784,6 +786,15 @@ struct pdg_handle {
 
 static std::string g_init_err;
 
+// NVTX range for profilers (nsys, ncu's NVTX filters): the entry points and,
+// in the plain form, each SCP iteration.  Costs nothing without a tool.
+struct NvtxRange {
+  explicit NvtxRange(const char* m) { nvtxRangePushA(m); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 #define PDG_CUDA(h, call)                                                        \
   do {                                                                           \
     cudaError_t e_ = (call);                                                     \
@@ -1126,6 +1137,7 @@ static int run_solve(pdg_handle* h, int B, const double* x0, const int* Ns, int 
   cudaGraphExec_t exec = h->plain_exec;
   int rc = 0;
   for (int j = 0; j < h->p.scp_jmax; ++j) {
+    NvtxRange r("pdg_mc plain SCP iteration");
     ce = cudaGraphLaunch(exec, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h->pinned_done, W.done, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -1453,6 +1465,8 @@ int pdg_mc_solve_batch(pdg_handle* h, int B, const double* x0, const int* n_node
   if (mode < 0 || mode > 2) return fail(h, PDG_EINVAL, "mode must be 0 (plain), 1 (persistent) or 2 (persistent, shape classes)");
   if (!x0 || !X || !U || !tf || !fuel || !status || !scp_iters || !pipg_iters) return fail(h, PDG_EINVAL, "NULL buffer");
   PDG_CUDA(h, cudaSetDevice(h->device));
+  NvtxRange r(mode == 0 ? "pdg_mc_solve_batch plain" : mode == 1 ? "pdg_mc_solve_batch persistent"
+                                                                   : "pdg_mc_solve_batch shape classes");
   return PDG_DISPATCH(h, run_solve, h, B, x0, n_nodes, mode, X, U, tf, fuel, status, scp_iters, pipg_iters, trace,
                       (cudaStream_t)cuda_stream);
 }
@@ -1490,6 +1504,7 @@ int pdg_mc_solve_batch_host(pdg_handle* h, int B, const double* x0, const int* n
   int* dsc = (int*)c; c += al(bi);
   long long* dpi = (long long*)c;
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  NvtxRange r("pdg_mc_solve_batch_host");
   PDG_CUDA(h, cudaMemcpyAsync(dx0, x0, bx0, cudaMemcpyHostToDevice, s));
   if (n_nodes) PDG_CUDA(h, cudaMemcpyAsync(dN, n_nodes, bN, cudaMemcpyHostToDevice, s));
   int rc = pdg_mc_solve_batch(h, B, dx0, n_nodes ? dN : nullptr, mode, dX, dU, dtf, dfu, dst, dsc, dpi, nullptr, s);
