@@ -37,10 +37,10 @@ METRIC = "converged PDG SCP solves/s on 1 GB300, batch 16384, N=15; % FP64/FP32 
 # hash (profiles/ has the summaries); reported only while the sources match.
 PROFILED_TRAFFIC = {
     # ncu (dram__bytes_read.sum, dram__bytes_write.sum) of k_persistent<double,4,1>:
-    # 6-DoF on 456 instances (one per CTA slot), 12.18 MB read + 66.32 MB written;
-    # 3-DoF on 608 instances at its tuned 128 threads, 2.646 MB read + 0.074 MB written
-    "78141bb1b0d64497": {("6dof", "fp64", 4, 15, "persistent"): 78.49e6 / 456,
-                         ("3dof", "fp64", 4, 15, "persistent"): 2.720e6 / 608},
+    # 6-DoF on 456 instances (one per CTA slot), 12.03 MB read + 71.16 MB written;
+    # 3-DoF on 608 instances at its tuned 128 threads, 3.056 MB read + 0.066 MB written
+    "3dc399354509043f": {("6dof", "fp64", 4, 15, "persistent"): 83.19e6 / 456,
+                         ("3dof", "fp64", 4, 15, "persistent"): 3.122e6 / 608},
 }
 
 
