@@ -79,8 +79,10 @@ def parse():
     ap.add_argument("--dt-min", type=float, default=0.0, help="Delta t_k lower bound (0: off)")
     ap.add_argument("--dt-max", type=float, default=0.0, help="Delta t_k upper bound (0: off)")
     ap.add_argument("--tf-max", type=float, default=0.0, help="final-time bound (0: off)")
-    ap.add_argument("--pipg-form", type=int, default=0, choices=[0, 1, 2],
-                    help="PIPG layout: 0 autotune cache / automatic, 1 shared memory, 2 registers")
+    ap.add_argument("--pipg-form", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="PIPG layout: 0 autotune cache / automatic, 1 shared memory, 2 registers, "
+                         "3 register tiles over lane groups")
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: autotune cache / automatic)")
     ap.add_argument("--err-sample", type=int, default=512,
                     help="fp32: instances re-solved in fp64 on the GPU to report the fp32 error (0: off)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic, at least 256)")
@@ -426,6 +428,9 @@ def run_ours(a):
         if S.tuned_form != a.pipg_form:  # cached threads were tuned for the other layout
             S.set_threads(0)
             S.tuned_threads = None
+    if a.threads:
+        S.set_threads(a.threads)
+        S.tuned_threads = None
     out = S.alloc_outputs(a.batch, dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2

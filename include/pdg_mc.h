@@ -228,17 +228,16 @@ int pdg_mc_grad_batch(pdg_handle* h, int B, const double* x0, const int* n_nodes
 int pdg_mc_launch_info(pdg_handle* h, int* threads, int* ctas_per_sm, int* smem_bytes);
 
 /* Override the threads-per-CTA of the solve kernels (multiple of 32 up to
- * 576, 0 = automatic).  Used by the autotuner.  The shared-memory PIPG form
- * runs at most 512; the register form needs at least one thread per dual row
- * plus the control lanes (see pdg_mc_set_pipg_form); a solve whose setting
- * does not fit returns PDG_EINVAL. */
+ * 576, 0 = automatic).  Used by the autotuner.  PIPG forms 1 and 3 run at
+ * most 512; forms 2 and 3 need a minimum (see pdg_mc_set_pipg_form); a solve
+ * whose setting does not fit returns PDG_EINVAL. */
 int pdg_mc_set_threads(pdg_handle* h, int threads);
 
 /* Autotune the launch shape for this handle's n_max, nu and precision on a
  * caller batch (no counterpart in the paper).  Times one solve of the batch
  * (device x0 [B][NX-1], n_nodes as in pdg_mc_solve_batch, execution mode 0/1/2)
- * for every candidate: PIPG form 1 at 128..512 threads and form 2 from the
- * threads it needs up to its limit, multiples of 32; candidates that do not
+ * for every candidate: PIPG form 1 at 128..512 threads, forms 2 and 3 from
+ * the threads they need up to their limits, multiples of 32; candidates that do not
  * fit on an SM are skipped.  Each candidate runs one untimed solve, then one
  * solve timed with CUDA events on cuda_stream, scored by converged solves per
  * second.  The fastest (form, threads) is applied to the handle (as by
@@ -258,11 +257,18 @@ int pdg_mc_autotune(pdg_handle* h, int B, const double* x0, const int* n_nodes, 
  *           the primal and dual steps go through shared memory.  Needs
  *           round32(NX (N-1)) + round32(N G) threads, G = 4 (nu = 4) or 8,
  *           at most 576 (FP32) or 512 (FP64);
- *   form 0: automatic (default) -- form 2 for FP32 when it fits, else form 1.
+ *   form 3: blocks padded to 16 x 16 (8 x 8 when NX <= 8) and cut into tiles
+ *           of 8 rows by 4 (2) columns, one tile per lane, so that a group
+ *           of 8 (4) lanes holds one interval's blocks and owns one node;
+ *           products run as packed pairs and their partial sums combine
+ *           by shuffles within the group.  Needs round32(8 N) threads
+ *           (round32(4 N) when NX <= 8), at least 64, at most 512;
+ *   form 0: automatic (default) -- form 3 for FP32 when the thread setting
+ *           allows it, else form 1.
  * Returns PDG_EINVAL for another value.  Synchronous; no device work. */
 int pdg_mc_set_pipg_form(pdg_handle* h, int form);
 
-/* The PIPG form (1 or 2) of the handle's last solve or SCP step, 0 before
+/* The PIPG form (1, 2 or 3) of the handle's last solve or SCP step, 0 before
  * the first; PDG_EINVAL for a NULL handle. */
 int pdg_mc_pipg_form(const pdg_handle* h);
 

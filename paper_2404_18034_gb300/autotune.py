@@ -3,8 +3,8 @@
 For one (device, n_max, nu, precision, execution form) the library's
 pdg_mc_autotune times a solve of a seeded batch at every candidate (PIPG
 layout, CTA size) pair -- the shared-memory PIPG form at 128..512 threads, the
-register form from the threads it needs up to its limit, candidates that do
-not fit skipped -- and keeps the fastest by converged solves per second; this
+register forms 2 and 3 from the threads they need up to their limits,
+candidates that do not fit skipped -- and keeps the fastest by converged solves per second; this
 module records the choice in a JSON cache keyed by
 "device|n_max|nu|precision|mode".  Solver(tune_cache=...) applies a cached
 choice through pdg_mc_set_pipg_form and pdg_mc_set_threads.  candidates()
@@ -59,11 +59,18 @@ def reg_threads(n_max: int, nu: int, model: str = "6dof") -> int:
     return round32((n_max - 1) * NXS[model]) + round32(n_max * (4 if nu <= 4 else 8))
 
 
-def candidates(n_max: int, nu: int, precision: int, forms: Iterable[int] = (1, 2),
+def ks_threads(n_max: int, model: str = "6dof") -> int:
+    """Threads PIPG form 3 needs (8 lanes per node, 4 when NX <= 8, whole
+    warps)."""
+    return round32(n_max * (4 if NXS[model] <= 8 else 8))
+
+
+def candidates(n_max: int, nu: int, precision: int, forms: Iterable[int] = (1, 2, 3),
                model: str = "6dof") -> Iterable[Tuple[int, int]]:
     """(form, CTA size) pairs with at least one discretization interval per
     wave whose shared-memory image fits on an SM (mirrors the kernel's layout
-    rule); the register form from its minimum up to 576 (FP32) or 512 threads."""
+    rule); form 2 from its minimum up to 576 (FP32) or 512 threads, form 3
+    from its minimum up to 512."""
     out = []
     if 1 in forms:
         out += [(1, t) for t in _fitting(range(128, 513, 32), n_max, nu, precision, model)]
@@ -71,6 +78,8 @@ def candidates(n_max: int, nu: int, precision: int, forms: Iterable[int] = (1, 2
         hi = 576 if precision == 1 else 512
         out += [(2, t) for t in _fitting(range(reg_threads(n_max, nu, model), hi + 1, 32), n_max, nu, precision,
                                          model)]
+    if 3 in forms:
+        out += [(3, t) for t in _fitting(range(ks_threads(n_max, model), 513, 32), n_max, nu, precision, model)]
     return out
 
 

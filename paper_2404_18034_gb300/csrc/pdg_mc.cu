@@ -39,9 +39,12 @@ using namespace pdg;
 #endif
 
 // PIPG forms: 1 = blocks in shared memory (phase_pipg), 2 = blocks and
-// iterates in registers (phase_pipg_reg).  The register form runs one thread
-// per dual row plus the control lanes, so its kernels are built for up to
-// PDG_REG_MAXT threads (FP32) or 512 (FP64).
+// iterates in registers (phase_pipg_reg), 3 = blocks in register tiles over
+// lane groups (phase_pipg_ks).  The register form runs one thread per dual
+// row plus the control lanes, so its kernels are built for up to
+// PDG_REG_MAXT threads (FP32) or 512 (FP64).  Form 3 is built for up to 512
+// threads and one CTA per SM, so its FP32 kernels may take 128 registers: four
+// CTAs per SM at N <= 16 (128 threads).
 #define PDG_REG_MAXT_F32 576
 // FP64 solve kernels: compiled for up to PDG_FP64_MAXT threads with at least
 // PDG_FP64_MINB CTAs per SM (the register budget is 65536 / (threads x CTAs))
@@ -53,7 +56,7 @@ using namespace pdg;
 #endif
 #define PDG_LB(R, PV)                                                                       \
   __launch_bounds__((PV) == 2 && sizeof(R) == 4 ? PDG_REG_MAXT_F32 : (sizeof(R) == 8 ? PDG_FP64_MAXT : 512), \
-                    sizeof(R) == 4 && (PV) != 2 ? PDG_FP32_MIN_BLOCKS : (sizeof(R) == 8 ? PDG_FP64_MINB : 1))
+                    sizeof(R) == 8 ? PDG_FP64_MINB : ((PV) == 1 ? PDG_FP32_MIN_BLOCKS : 1))
 
 namespace {
 
@@ -61,6 +64,7 @@ template <typename R, int NU, int PV, bool CK = false>
 __device__ __forceinline__ int run_pipg(const DParams& P, const Lay& L, R* sm, R sigma, int force,
                                         double* ck = nullptr) {
   if constexpr (PV == 2) return phase_pipg_reg<R, NU>(P, L, sm, sigma, force);
+  else if constexpr (PV == 3) return phase_pipg_ks<R, NU>(P, L, sm, sigma, force);
   else return phase_pipg<R, NU, CK>(P, L, sm, sigma, force, ck);
 }
 
@@ -911,24 +915,26 @@ static int threads_for(int N, int nu, int precision) {
 }
 
 // PIPG form and CTA size for instances of up to N nodes.  Auto (variant 0):
-// FP32 takes the register form when its threads fit (its shared-memory form
-// is bound by shared-memory bandwidth), FP64 the shared-memory form (bound by
-// the FP64 pipe, it gains nothing from registers and keeps three CTAs per SM).
-// In auto mode a thread-count override below what the register form needs
-// selects the shared form; with the register form requested it is an error.
+// FP32 takes the tiled register form (form 3; the shared-memory form is bound
+// by shared-memory bandwidth, form 2 by its operand loads), FP64 the
+// shared-memory form (bound by the FP64 pipe, it gains nothing from registers
+// and keeps three CTAs per SM).  In auto mode a thread-count override outside
+// what form 3 accepts selects the shared form; with form 2 or 3 requested it
+// is an error.
 // The non-PIPG kernels of the plain form run with at most 512 threads.
 struct Plan {
   int T;   // threads of the solve kernel (and of k_plain_pipg)
   int Tr;  // threads of the other plain-form kernels
-  int pv;  // 1 shared-memory PIPG, 2 register PIPG
+  int pv;  // 1 shared-memory PIPG, 2 register PIPG, 3 register tiles
 };
 
 static bool plan_for(const pdg_handle* h, int N, Plan* out, std::string* why, bool use_override = true) {
   const int treg = pipg_reg_threads(N, h->p.nu);
   const int maxt = h->p.precision == 1 ? PDG_REG_MAXT_F32 : 512;
   const int ov = use_override ? h->threads_override : 0;
+  const int tks = pipg_ks_threads(N);
   int pv = h->pipg_variant;
-  if (pv == 0) pv = (h->p.precision == 1 && treg <= maxt && (ov == 0 || ov >= treg)) ? 2 : 1;
+  if (pv == 0) pv = (h->p.precision == 1 && tks <= 512 && (ov == 0 || (ov >= tks && ov <= 512))) ? 3 : 1;
   if (pv == 2) {
     const int T = ov > 0 ? ov : treg;
     if (T < treg || T > maxt) {
@@ -937,6 +943,15 @@ static bool plan_for(const pdg_handle* h, int N, Plan* out, std::string* why, bo
       return false;
     }
     *out = {T, T < 512 ? T : 512, 2};
+  } else if (pv == 3) {
+    // the lane groups' threads, at least two warps (the discretization wants
+    // one interval per wave); the plain form's other kernels at least 128
+    const int T = ov > 0 ? ov : (tks < 64 ? 64 : tks);
+    if (T < tks || T > 512) {
+      *why = "PIPG form 3 needs " + std::to_string(tks) + " to 512 threads per CTA at N = " + std::to_string(N);
+      return false;
+    }
+    *out = {T, T < 128 ? 128 : T, 3};
   } else {
     const int T = ov > 0 ? ov : threads_for(N, h->p.nu, h->p.precision);
     if (T > 512) { *why = "the shared-memory PIPG form runs at most 512 threads per CTA"; return false; }
@@ -955,18 +970,21 @@ static PersistentFn<R, NU> persistent_fn(int pv, bool ck = false) {
   if constexpr (sizeof(R) == 8) {
     if (ck && pv == 1) return k_persistent<R, NU, 1, true>;
   }
-  return pv == 2 ? k_persistent<R, NU, 2> : k_persistent<R, NU, 1>;
+  return pv == 3 ? k_persistent<R, NU, 3> : (pv == 2 ? k_persistent<R, NU, 2> : k_persistent<R, NU, 1>);
 }
 template <typename R, int NU>
-static PlainPipgFn<R, NU> plain_pipg_fn(int pv) { return pv == 2 ? k_plain_pipg<R, NU, 2> : k_plain_pipg<R, NU, 1>; }
+static PlainPipgFn<R, NU> plain_pipg_fn(int pv) {
+  return pv == 3 ? k_plain_pipg<R, NU, 3> : (pv == 2 ? k_plain_pipg<R, NU, 2> : k_plain_pipg<R, NU, 1>);
+}
 
 template <typename R, int NU>
 struct Kern {
   static int prepare(pdg_handle* h, int threads, size_t smem) {
     const void* fns[] = {(const void*)k_persistent<R, NU, 1>, (const void*)k_persistent<R, NU, 2>,
-                         (const void*)k_plain_init<R, NU>, (const void*)k_plain_disc<R, NU>,
-                         (const void*)k_plain_power<R, NU>, (const void*)k_plain_pipg<R, NU, 1>,
-                         (const void*)k_plain_pipg<R, NU, 2>, (const void*)k_plain_update<R, NU>,
+                         (const void*)k_persistent<R, NU, 3>, (const void*)k_plain_init<R, NU>,
+                         (const void*)k_plain_disc<R, NU>, (const void*)k_plain_power<R, NU>,
+                         (const void*)k_plain_pipg<R, NU, 1>, (const void*)k_plain_pipg<R, NU, 2>,
+                         (const void*)k_plain_pipg<R, NU, 3>, (const void*)k_plain_update<R, NU>,
                          (const void*)k_subproblem<R, NU>};
     for (const void* f : fns) PDG_CUDA(h, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if constexpr (sizeof(R) == 8)
@@ -1407,7 +1425,6 @@ int pdg_mc_init(const pdg_params* p, int n_max, pdg_handle** out) {
     }
     if (ea != cudaSuccess) {
       if (h->abort_host) cudaFreeHost(h->abort_host);
-  if (h->plain_exec) cudaGraphExecDestroy(h->plain_exec);
       delete h;
       g_init_err = std::string("abort word (mapped pinned host memory): ") + cudaGetErrorString(ea);
       return PDG_ECUDA;
@@ -1555,7 +1572,8 @@ int pdg_mc_launch_info(pdg_handle* h, int* threads, int* ctas_per_sm, int* smem_
 
 int pdg_mc_set_pipg_form(pdg_handle* h, int form) {
   if (!h) return PDG_EINVAL;
-  if (form < 0 || form > 2) return fail(h, PDG_EINVAL, "PIPG form must be 0 (auto), 1 (shared memory) or 2 (registers)");
+  if (form < 0 || form > 3)
+    return fail(h, PDG_EINVAL, "PIPG form must be 0 (auto), 1 (shared memory), 2 (registers) or 3 (register tiles)");
   h->pipg_variant = form;
   return PDG_OK;
 }
@@ -1593,9 +1611,11 @@ int pdg_mc_autotune(pdg_handle* h, int B, const double* x0, const int* n_nodes, 
   double best = -1.0;
   int best_t = 0, best_f = 0, rc = PDG_OK;
   const int treg = pipg_reg_threads(n, nu), maxt = h->p.precision == 1 ? PDG_REG_MAXT_F32 : 512;
-  // candidates: (form 1, 128..512) and (form 2, its minimum .. its limit), multiples of 32
-  for (int form = 1; form <= 2 && rc == PDG_OK; ++form) {
-    const int t_lo = form == 1 ? 128 : treg, t_hi = form == 1 ? 512 : maxt;
+  const int tks = pipg_ks_threads(n);
+  // candidates: (form 1, 128..512), (form 2, its minimum .. its limit) and
+  // (form 3, its minimum .. 512), multiples of 32
+  for (int form = 1; form <= 3 && rc == PDG_OK; ++form) {
+    const int t_lo = form == 1 ? 128 : (form == 2 ? treg : tks), t_hi = form == 2 ? maxt : 512;
     for (int T = t_lo; T <= t_hi && rc == PDG_OK; T += 32) {
       h->pipg_variant = form;
       h->threads_override = T;

@@ -944,6 +944,485 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
   return j > jmax ? jmax : j;
 }
 
+// ---------------------------------------------------------------------------
+// PIPG_custom with each interval's blocks cut into tiles over a group of
+// lanes (form 3).
+//
+// The same iteration as phase_pipg and phase_pipg_reg (Alg. PIPG_custom with
+// the stop test of Alg. stopping).  Node vectors are padded to KS_NXB entries
+// (16, or 8 when NX <= 8) and a block to KS_NXB x KS_NXB, cut into tiles of
+// KS_TR = 8 rows by KS_TC columns (4, or 2 when NX <= 8).  Group g, KS_GS =
+// KS_NR x KS_NC consecutive lanes, owns interval g and node g; its lane
+// (rb, cb) = (l / KS_NC, l % KS_NC) keeps, in registers,
+//  * tile (rb, cb) of hat A^-_g (zero outside NX, and for the last node,
+//    which has no interval), as pairs of rows;
+//  * the tile's rows of hat B^-_g and hat B^+_g in the control columns
+//    cb + KS_NC s.
+// One tile serves both products of an iteration: A^T phi~ in the primal step
+// and A (2 x - x~) in the dual step.  A tile's partial sums are combined over
+// the lanes of its tile column (primal) or tile row (dual) by butterfly
+// shuffles that leave each lane the full sums of KS_WC columns (KS_WR rows);
+// that lane owns those x components (dual rows).  The control sums are
+// combined on every lane of a tile column, so each of them holds the node's
+// controls.  What stays inside a group (phi~_g, the extrapolated x_g and u_g)
+// moves by shuffles.  Shared memory carries what the neighbouring groups
+// read: phi~_g and hat B^+_g^T phi~_g into the primal step of group g+1, the
+// extrapolated x_{g+1} and u_{g+1} into the dual step of group g, and the
+// relaxed CTCS duals.  Products run as packed pairs (two FP32 FMAs in one
+// instruction on sm_100 and later).
+// Needs blockDim.x >= pipg_ks_threads(N).
+// ---------------------------------------------------------------------------
+constexpr int KS_NXB = NX <= 8 ? 8 : 16;  // node vectors padded to whole tiles
+constexpr int KS_TR = 8;                  // tile rows
+constexpr int KS_TC = NX <= 8 ? 2 : 4;    // tile columns
+constexpr int KS_NR = KS_NXB / KS_TR;     // tile rows per block (lanes of a tile column)
+constexpr int KS_NC = KS_NXB / KS_TC;     // tile columns per block (lanes of a tile row)
+constexpr int KS_GS = KS_NR * KS_NC;      // lanes per group
+constexpr int KS_WR = KS_TR / KS_NC;      // dual rows a lane owns
+constexpr int KS_WC = KS_TC / KS_NR;      // x components a lane owns
+static_assert(KS_WR >= 1 && KS_WC >= 1 && 32 % KS_GS == 0, "tile shape");
+__host__ __device__ inline int pipg_ks_threads(int N) { return round32(N * KS_GS); }
+
+// Shared-memory offsets (inside the phase-local union region, 16-byte
+// aligned): vp[N][KS_NXB] (phi~ per interval), dx[N][KS_NXB], du[N][nup],
+// bq[N][nup] (hat B^+_{g-1}^T phi~_{g-1}, the control gradient node g gets
+// from interval g-1), th[N] (theta~ per interval; th[N-1] stays zero).
+struct KsLay { int vp, dx, du, bq, th, end; };
+__host__ __device__ inline KsLay make_ks_lay(const Lay& L) {
+  const int nup = KS_NC * ((L.nu + KS_NC - 1) / KS_NC);
+  KsLay Q;
+  int o = (L.xt + 3) & ~3;
+  Q.vp = o; o += L.N * KS_NXB;
+  Q.dx = o; o += L.N * KS_NXB;
+  Q.du = o; o += (L.N * nup + 3) & ~3;
+  Q.bq = o; o += (L.N * nup + 3) & ~3;
+  Q.th = o; o += (L.N + 3) & ~3;
+  Q.end = o;
+  return Q;
+}
+
+// Two values in one register pair: FP32 uses the packed FMA of sm_100 and
+// later, FP64 two scalar FMAs.
+template <typename R> struct Pr;
+template <> struct Pr<float> {
+  using T = float2;
+  __device__ __forceinline__ static T mk(float a, float b) { return make_float2(a, b); }
+  __device__ __forceinline__ static T mul(T a, T b) { return __fmul2_rn(a, b); }
+  __device__ __forceinline__ static T fma(T a, T b, T c) { return __ffma2_rn(a, b, c); }
+};
+template <> struct Pr<double> {
+  struct T { double x, y; };
+  __device__ __forceinline__ static T mk(double a, double b) { return T{a, b}; }
+  __device__ __forceinline__ static T mul(T a, T b) { return T{a.x * b.x, a.y * b.y}; }
+  __device__ __forceinline__ static T fma(T a, T b, T c) { return T{::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)}; }
+};
+
+// Butterflies over the M lanes sel = 0..M-1 at stride S (M = 1, 2 or 4).  A
+// lane keeps its n partial sums in an order of its own: stored entry s is
+// entry s ^ ks_perm<M, n>(sel).  Then every reduce round keeps the first half
+// of the stored entries and sends the second half (no per-lane selection),
+// and ks_reduce_scatter leaves lane sel the full sums of entries
+// (n / M) sel .. (n / M) sel + n / M - 1, in order.  ks_all_gather is its
+// inverse and returns the n entries in the lane's stored order.
+template <int M, int n>
+__host__ __device__ constexpr int ks_perm(int sel) {
+  return M == 4 ? (n / 2) * ((sel >> 1) & 1) + (n / 4) * (sel & 1) : (M == 2 ? (n / 2) * (sel & 1) : 0);
+}
+template <int n, int S, typename R>
+__device__ __forceinline__ void ks_rs_round(const R (&v)[n], R (&o)[n / 2]) {
+#pragma unroll
+  for (int e = 0; e < n / 2; ++e) o[e] = v[e] + __shfl_xor_sync(0xffffffffu, v[n / 2 + e], S);
+}
+template <int n, int S, typename R>
+__device__ __forceinline__ void ks_ag_round(const R (&o)[n], R (&v)[2 * n]) {
+#pragma unroll
+  for (int e = 0; e < n; ++e) {
+    v[e] = o[e];
+    v[n + e] = __shfl_xor_sync(0xffffffffu, o[e], S);
+  }
+}
+template <int M, int S, int n, typename R>
+__device__ __forceinline__ void ks_reduce_scatter(const R (&v)[n], R (&o)[n / M]) {
+  if constexpr (M == 1) {
+#pragma unroll
+    for (int e = 0; e < n; ++e) o[e] = v[e];
+  } else if constexpr (M == 2) {
+    ks_rs_round<n, S>(v, o);
+  } else {
+    static_assert(M == 4, "groups of 1, 2 or 4 lanes");
+    R t[n / 2];
+    ks_rs_round<n, 2 * S>(v, t);
+    ks_rs_round<n / 2, S>(t, o);
+  }
+}
+template <int M, int S, int n, typename R>
+__device__ __forceinline__ void ks_all_gather(const R (&o)[n / M], R (&v)[n]) {
+  if constexpr (M == 1) {
+#pragma unroll
+    for (int e = 0; e < n; ++e) v[e] = o[e];
+  } else if constexpr (M == 2) {
+    ks_ag_round<n / 2, S>(o, v);
+  } else {
+    static_assert(M == 4, "groups of 1, 2 or 4 lanes");
+    R t[n / 2];
+    ks_ag_round<n / 4, S>(o, t);
+    ks_ag_round<n / 2, 2 * S>(t, v);
+  }
+}
+// every lane of the M gets the same sum (IEEE addition commutes, so the lanes
+// agree bit for bit)
+template <int M, int S, typename R>
+__device__ __forceinline__ R ks_all_sum(R x) {
+  if constexpr (M >= 2) x += __shfl_xor_sync(0xffffffffu, x, S);
+  if constexpr (M >= 4) x += __shfl_xor_sync(0xffffffffu, x, 2 * S);
+  return x;
+}
+
+#ifdef PDG_PIPG_KS_NOINLINE
+#define PDG_PKS_ATTR __noinline__
+#else
+#define PDG_PKS_ATTR __forceinline__
+#endif
+template <typename R, int NU>
+__device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*image*/, R sigma, int force) {
+  using OB = OrdBits<R>;
+  using U = typename OB::U;
+  using PR = Pr<R>;
+  using T2 = typename PR::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* const sm = reinterpret_cast<R*>(smraw);
+  constexpr int NXB = KS_NXB, TR = KS_TR, TC = KS_TC, NR = KS_NR, NCB = KS_NC, GS = KS_GS;
+  constexpr int WR = KS_WR, WC = KS_WC, TH = TR / 2;
+  constexpr int NC = (NU + NCB - 1) / NCB;  // control columns per lane
+  constexpr int NUP = NCB * NC;
+  const int N = L.N, tid = threadIdx.x;
+  const KsLay Q = make_ks_lay(L);
+  R* const vps = sm + Q.vp;
+  R* const dxs = sm + Q.dx;
+  R* const dus = sm + Q.du;
+  R* const bqs = sm + Q.bq;
+  R* const ths = sm + Q.th;
+  const int g = tid / GS, ln = tid - GS * (tid / GS);
+  const int rb = ln / NCB, cb = ln - NCB * (ln / NCB);
+  // whole warps past the last group only join the barriers; lanes of a group
+  // past the last one in a live warp join the shuffles, read clamped
+  // addresses and store nothing
+  const bool wlive = (tid & ~31) < N * GS;
+  const bool live = g < N;
+  const bool has_iv = g < N - 1;
+  const int gv = live ? g : N - 1;
+  const int gm1 = gv > 0 ? gv - 1 : 0, gp1 = gv < N - 1 ? gv + 1 : gv;
+  const R wp = R(P.w_prox);
+  const R alpha = R(2) / (wp + sqrt(wp * wp + R(4) * R(P.omega) * sigma));
+  const R beta = R(P.omega) * alpha;
+  const R c1 = R(1) - alpha * wp;
+  const R rho = R(P.rho);
+  const R rhb = rho * beta;
+  const R aw = alpha * R(P.w_ep);  // virtual-control iterates kept shifted (see phase_pipg)
+  const R omr = R(1) - rho, raw = rho * aw;
+  for (int t = tid; t < Q.end - Q.vp; t += blockDim.x) sm[Q.vp + t] = R(0);
+  // ---- tiles, in the lane's stored order (rows permuted by its place in the
+  // tile row, columns by its place in the tile column; see ks_perm), as pairs
+  // of stored rows 2h, 2h+1
+  const int prow = ks_perm<NCB, TR>(cb), pcol = ks_perm<NR, TC>(rb);
+  T2 ap[TH][TC], bm[TH][NC], bp[TH][NC];
+#pragma unroll
+  for (int h = 0; h < TH; ++h) {
+    const int r0 = TR * rb + ((2 * h) ^ prow), r1 = TR * rb + ((2 * h + 1) ^ prow);
+#pragma unroll
+    for (int q = 0; q < TC; ++q) {
+      const int c = TC * cb + (q ^ pcol);
+      const bool okc = has_iv && c < NX;
+      ap[h][q] = PR::mk((okc && r0 < NX) ? sm[L.Am + (g * NX + r0) * NX + c] : R(0),
+                        (okc && r1 < NX) ? sm[L.Am + (g * NX + r1) * NX + c] : R(0));
+    }
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      const int cc = cb + NCB * s;
+      const bool okc = has_iv && cc < NU;
+      bm[h][s] = PR::mk((okc && r0 < NX) ? sm[L.Bm + (g * NX + r0) * NU + cc] : R(0),
+                        (okc && r1 < NX) ? sm[L.Bm + (g * NX + r1) * NU + cc] : R(0));
+      bp[h][s] = PR::mk((okc && r0 < NX) ? sm[L.Bp + (g * NX + r0) * NU + cc] : R(0),
+                        (okc && r1 < NX) ? sm[L.Bp + (g * NX + r1) * NU + cc] : R(0));
+    }
+  }
+  // ---- iterates.  x components TC cb + WC rb + e of node g, dual rows
+  // TR rb + WR cb + e of interval g, controls cb + NCB s of node g (on every
+  // lane of the tile column)
+  R xt[WC], xh[WC], zfx[WC], dxn[WC];
+  bool fx[WC], okx[WC], okd[WR];
+  R nvp[WR], nvm[WR], mup[WR], mum[WR], ft[WR], fh[WR], wv[WR];
+  R ut[NC], uh[NC], tref[NC], dun[NC];
+  T2 fg[TH];
+#pragma unroll
+  for (int e = 0; e < WC; ++e) {
+    const int c = TC * cb + WC * rb + e;
+    okx[e] = live && c < NX;
+    xt[e] = xh[e] = okx[e] ? sm[L.xh + g * NX + c] : R(0);
+    fx[e] = okx[e] && (g == 0 || (g == N - 1 && P.fix_f[c]));
+    zfx[e] = !okx[e] ? R(0) : (g == 0 ? sm[L.zi + c] : (fx[e] ? sm[L.zf + c] : R(0)));
+    dxn[e] = 0;
+  }
+#pragma unroll
+  for (int e = 0; e < WR; ++e) {
+    const int i = TR * rb + WR * cb + e;
+    okd[e] = has_iv && i < NX;
+    const int o = g * NX + i;
+    wv[e] = okd[e] ? sm[L.w + o] : R(0);
+    mup[e] = okd[e] ? sm[L.mup + o] : R(0);
+    mum[e] = okd[e] ? sm[L.mum + o] : R(0);
+    nvp[e] = okd[e] ? mup[e] - aw : R(0);
+    nvm[e] = okd[e] ? mum[e] - aw : R(0);
+    ft[e] = fh[e] = okd[e] ? sm[L.phi + o] : R(0);
+  }
+#pragma unroll
+  for (int h = 0; h < TH; ++h) {
+    const int r0 = TR * rb + ((2 * h) ^ prow), r1 = TR * rb + ((2 * h + 1) ^ prow);
+    fg[h] = PR::mk((has_iv && r0 < NX) ? sm[L.phi + g * NX + r0] : R(0),
+                   (has_iv && r1 < NX) ? sm[L.phi + g * NX + r1] : R(0));
+  }
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    const int cc = cb + NCB * s;
+    const bool ok = live && cc < NU;
+    ut[s] = uh[s] = ok ? sm[L.uh + g * NU + cc] : R(0);
+    tref[s] = (ok && cc < 3) ? sm[L.Ub + g * NU + cc] : R(0);
+    dun[s] = 0;
+  }
+  const R lo = sm[L.lo + gv], hi = sm[L.hi + gv];
+  // the lane that owns dual row IY of interval g also owns theta_g
+  const int iy0 = TR * rb + WR * cb;
+  const bool th_lane = has_iv && IY >= iy0 && IY < iy0 + WR;
+  R tht = 0, thh = 0, eps = 0;
+  if (th_lane) { tht = thh = sm[L.th + g]; eps = sm[L.eps + g]; }
+  __syncthreads();  // the exchange region is zero
+#pragma unroll
+  for (int e = 0; e < WR; ++e)
+    if (okd[e]) vps[g * NXB + TR * rb + WR * cb + e] = ft[e];
+  for (int t = tid; t < N - 1; t += blockDim.x) ths[t] = sm[L.th + t];
+  // hat B^+_g^T phi~_g for node g+1, summed over the tile column
+  auto bq_out = [&]() {
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      T2 acc = PR::mul(bp[0][s], fg[0]);
+#pragma unroll
+      for (int h = 1; h < TH; ++h) acc = PR::fma(bp[h][s], fg[h], acc);
+      const R v = ks_all_sum<NR, NCB>(acc.x + acc.y);
+      if (has_iv && rb == 0 && cb + NCB * s < NU) bqs[(g + 1) * NUP + cb + NCB * s] = v;
+    }
+  };
+  if (wlive) bq_out();
+  __syncthreads();
+  const R sa = R(P.soc_tan), tmax = R(P.T_max), pT = R(P.Pu[0]), ipT = R(P.Puinv[0]);
+  const R acost = alpha * R(P.w_cost);
+  const int jmax = force > 0 ? force : P.pipg_jmax;
+  const int jcheck = P.pipg_jcheck;
+  auto iterate = [&](auto chk_tag) -> bool {
+    constexpr bool chk = decltype(chk_tag)::value;
+    U zn = 0, zo = 0, zd = 0, rn = 0, ro = 0, rd = 0;
+    // ---- projected gradient step (primal)
+    if (wlive) {
+      R cx[TC], cu[NC];
+#pragma unroll
+      for (int q = 0; q < TC; ++q) {
+        T2 acc = PR::mul(ap[0][q], fg[0]);
+#pragma unroll
+        for (int h = 1; h < TH; ++h) acc = PR::fma(ap[h][q], fg[h], acc);
+        cx[q] = acc.x + acc.y;
+      }
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        T2 acc = PR::mul(bm[0][s], fg[0]);
+#pragma unroll
+        for (int h = 1; h < TH; ++h) acc = PR::fma(bm[h][s], fg[h], acc);
+        cu[s] = ks_all_sum<NR, NCB>(acc.x + acc.y) + bqs[gv * NUP + cb + NCB * s];
+      }
+      R gx[WC];
+      ks_reduce_scatter<NR, NCB>(cx, gx);
+      const R tdv = ths[gm1] - ths[gv];  // theta~_{g-1} - theta~_g (th[N-1] = 0)
+#pragma unroll
+      for (int e = 0; e < WC; ++e) {
+        const int c = TC * cb + WC * rb + e;  // padding entries of vp read as zero
+        const R G = fma(c == IY ? R(1) : R(0), tdv, gx[e] - vps[gm1 * NXB + c]);
+        const R cost = (g == N - 1 && c == IM) ? acost : R(0);
+        R xn = fma(-alpha, G, fma(c1, xt[e], cost));
+        xn = fx[e] ? zfx[e] : xn;
+        dxn[e] = fma(R(2), xn, -xt[e]);
+        if (okx[e]) dxs[g * NXB + c] = dxn[e];
+        xt[e] += rho * (xn - xt[e]);
+        if constexpr (chk) {
+          if (okx[e]) { zn = umax(zn, OB::abs(xn)); zo = umax(zo, OB::abs(xh[e])); zd = umax(zd, OB::abs(xn - xh[e])); }
+        }
+        xh[e] = xn;
+      }
+      R un[NC];
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        const int cc = cb + NCB * s;
+        un[s] = c1 * ut[s] - alpha * cu[s];
+        if (cc == NU - 1) un[s] = rmin(rmax(un[s], lo), hi);
+      }
+      if (P.soc) {
+        // the node's thrust onto the sector (cone about body x, then the
+        // ball); component cc sits on lane cc % NCB of this tile row, in
+        // control column cc / NCB, and every tile row projects alike
+        const int base = (tid & 31) & ~(NCB - 1);
+        R tv[NC];
+#pragma unroll
+        for (int s = 0; s < NC; ++s) tv[s] = (cb + NCB * s < 3) ? tref[s] + pT * un[s] : R(0);
+        R T0 = __shfl_sync(0xffffffffu, tv[0], base);
+        R T1 = __shfl_sync(0xffffffffu, tv[1 / NCB], base + 1 % NCB);
+        R T2v = __shfl_sync(0xffffffffu, tv[2 / NCB], base + 2 % NCB);
+        const R rr = ::sqrt(T1 * T1 + T2v * T2v);
+        if (rr > sa * T0) {
+          if (sa * rr <= -T0) {
+            T0 = 0; T1 = 0; T2v = 0;
+          } else {
+            const R tp = (T0 + sa * rr) / (R(1) + sa * sa);
+            const R sc = sa * tp / rr;
+            T0 = tp; T1 *= sc; T2v *= sc;
+          }
+        }
+        const R nT = ::sqrt(T0 * T0 + T1 * T1 + T2v * T2v);
+        if (nT > tmax) { const R f = tmax / nT; T0 *= f; T1 *= f; T2v *= f; }
+#pragma unroll
+        for (int s = 0; s < NC; ++s) {
+          const int cc = cb + NCB * s;
+          if (cc < 3) un[s] = ((cc == 0 ? T0 : (cc == 1 ? T1 : T2v)) - tref[s]) * ipT;
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        const int cc = cb + NCB * s;
+        const bool ok = live && cc < NU;
+        dun[s] = fma(R(2), un[s], -ut[s]);
+        if (ok && rb == 0) dus[g * NUP + cc] = dun[s];
+        ut[s] += rho * (un[s] - ut[s]);
+        if constexpr (chk) {
+          if (ok) { zn = umax(zn, OB::abs(un[s])); zo = umax(zo, OB::abs(uh[s])); zd = umax(zd, OB::abs(un[s] - uh[s])); }
+        }
+        uh[s] = un[s];
+      }
+    }
+    __syncthreads();
+    // ---- virtual controls and proportional-integral feedback (dual)
+    if (wlive) {
+      R dc[TC], rr[TR];
+      ks_all_gather<NR, NCB>(dxn, dc);
+      T2 du0[NC], du1[NC];
+#pragma unroll
+      for (int s = 0; s < NC; ++s) {
+        const R v1 = dus[gp1 * NUP + cb + NCB * s];
+        du0[s] = PR::mk(dun[s], dun[s]);
+        du1[s] = PR::mk(v1, v1);
+      }
+#pragma unroll
+      for (int h = 0; h < TH; ++h) {
+        T2 acc = PR::mul(ap[h][0], PR::mk(dc[0], dc[0]));
+#pragma unroll
+        for (int q = 1; q < TC; ++q) acc = PR::fma(ap[h][q], PR::mk(dc[q], dc[q]), acc);
+#pragma unroll
+        for (int s = 0; s < NC; ++s) { acc = PR::fma(bm[h][s], du0[s], acc); acc = PR::fma(bp[h][s], du1[s], acc); }
+        rr[2 * h] = acc.x;
+        rr[2 * h + 1] = acc.y;
+      }
+      R rs[WR];
+      ks_reduce_scatter<NCB, 1>(rr, rs);
+#pragma unroll
+      for (int e = 0; e < WR; ++e) {
+        const int i = TR * rb + WR * cb + e;  // padding entries of dx read as zero
+        const R f = ft[e], va = nvp[e], vb = nvm[e];
+        const R mp = max0(va - alpha * f);
+        const R mm = max0(vb + alpha * f);
+        nvp[e] = omr * va + (rho * mp - raw);
+        nvm[e] = omr * vb + (rho * mm - raw);
+        if constexpr (chk) {
+          if (okd[e]) {
+            zn = umax(zn, umax(OB::nonneg(mp), OB::nonneg(mm)));
+            zo = umax(zo, umax(OB::nonneg(mup[e]), OB::nonneg(mum[e])));
+            zd = umax(zd, umax(OB::abs(mp - mup[e]), OB::abs(mm - mum[e])));
+          }
+        }
+        mup[e] = mp;
+        mum[e] = mm;
+        const R r0 = wv[e] + (fma(R(2), mp, -va) - fma(R(2), mm, -vb)) - dxs[gp1 * NXB + i] + rs[e];
+        const R r = okd[e] ? r0 : R(0);  // rows that do not exist keep phi~ = 0
+        const R pn = f + beta * r;
+        ft[e] = f + rhb * r;  // = phi~ + rho (phi_new - phi~)
+        if constexpr (chk) {
+          if (okd[e]) { rn = umax(rn, OB::abs(pn)); ro = umax(ro, OB::abs(fh[e])); rd = umax(rd, OB::abs(pn - fh[e])); }
+        }
+        fh[e] = pn;
+        if (okd[e]) vps[g * NXB + i] = ft[e];
+      }
+      {
+        R fv[TR];
+        ks_all_gather<NCB, 1>(ft, fv);
+#pragma unroll
+        for (int h = 0; h < TH; ++h) fg[h] = PR::mk(fv[2 * h], fv[2 * h + 1]);
+      }
+      bq_out();
+      if (th_lane) {
+        const R hy = dxs[gp1 * NXB + IY] - dxs[g * NXB + IY] - eps;
+        const R tn = max0(tht + beta * hy);
+        tht += rho * (tn - tht);
+        if constexpr (chk) { rn = umax(rn, OB::nonneg(tn)); ro = umax(ro, OB::abs(thh)); rd = umax(rd, OB::abs(tn - thh)); }
+        thh = tn;
+        ths[g] = tht;
+      }
+    }
+    if constexpr (chk) {
+      U w6[6] = {zn, zo, zd, rn, ro, rd};
+      block_max_u<U, 6>(w6, reinterpret_cast<U*>(sm + L.red));
+      const R eabs = R(P.eps_abs), erel = R(P.eps_rel);
+      return OB::val(w6[2]) <= eabs + erel * rmax(OB::val(w6[0]), OB::val(w6[1])) &&
+             OB::val(w6[5]) <= eabs + erel * rmax(OB::val(w6[3]), OB::val(w6[4]));
+    } else {
+      (void)zn; (void)zo; (void)zd; (void)rn; (void)ro; (void)rd;
+      __syncthreads();
+      return false;
+    }
+  };
+  // blocks of jcheck iterations whose last one runs the stop test, so that
+  // the loop carries no per-iteration remainder
+  const bool chk_on = force <= 0 && jcheck > 0;
+  const int per = chk_on ? jcheck : (jmax > 0 ? jmax : 1);
+  int j = 0;
+  while (j < jmax) {
+    const int nb = per < jmax - j ? per : jmax - j;
+    for (int k = 1; k < nb; ++k) iterate(ChkTag<false>{});
+    j += nb;
+    if (chk_on && nb == per) {
+      if (iterate(ChkTag<true>{})) break;
+    } else {
+      iterate(ChkTag<false>{});
+    }
+  }
+  // iterates back to the image (warm start of the next SCP iteration)
+  if (wlive) {
+#pragma unroll
+    for (int e = 0; e < WC; ++e)
+      if (okx[e]) sm[L.xh + g * NX + TC * cb + WC * rb + e] = xh[e];
+#pragma unroll
+    for (int e = 0; e < WR; ++e) {
+      const int i = TR * rb + WR * cb + e;
+      if (okd[e]) {
+        sm[L.mup + g * NX + i] = mup[e];
+        sm[L.mum + g * NX + i] = mum[e];
+        sm[L.phi + g * NX + i] = fh[e];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      const int cc = cb + NCB * s;
+      if (live && cc < NU && rb == 0) sm[L.uh + g * NU + cc] = uh[s];
+    }
+    if (th_lane) sm[L.th + g] = thh;
+  }
+  __syncthreads();
+  return j;
+}
+
 // SCP update (Sec. 2.3.2: x = P_x x_hat + xbar) and convergence test
 // (reading: scaled step, scaled defect and CTCS budget).  Returns the scaled
 // step; *nonfinite is set when X or U holds a non-finite value.

@@ -354,7 +354,8 @@ class Solver:
         self._check(self.lib.pdg_mc_clear_abort(self.h), "pdg_mc_clear_abort")
 
     def set_pipg_form(self, form: int):
-        """0 automatic, 1 blocks in shared memory, 2 blocks in registers."""
+        """0 automatic, 1 blocks in shared memory, 2 blocks in registers,
+        3 blocks in register tiles over lane groups."""
         self._check(self.lib.pdg_mc_set_pipg_form(self.h, int(form)), "pdg_mc_set_pipg_form")
 
     def set_threads(self, threads: int):

@@ -1,6 +1,6 @@
 // layout_probe.cu -- test infrastructure: checks on the host that the
 // per-instance shared-memory layouts of the solver (make_lay, make_reg_lay,
-// make_adj) hold every region the kernels index, for every node count,
+// make_ks_lay, make_adj) hold every region the kernels index, for every node count,
 // control size and CTA size the library accepts.  Built by
 // tests/test_layout.py once per model; prints "OK <cases>" or the failures.
 #include <cstdio>
@@ -48,6 +48,17 @@ int main() {
           CHECK(Q.vp % 4 == 0 && Q.dx % 4 == 0 && Q.du % 4 == 0 && NXS % 4 == 0 && NXS >= NX, N, nu, T);
           CHECK(Q.dx - Q.vp == (N - 1) * NXS && Q.du - Q.dx == N * NXS && Q.td - Q.du >= N * nu, N, nu, T);
           CHECK(Q.end - Q.td >= N, N, nu, T);
+        }
+        // PIPG form 3 (register tiles over lane groups) where its thread rule is met
+        if (T >= pipg_ks_threads(N) && T <= 512) {
+          const KsLay Q = make_ks_lay(L);
+          const int nup = KS_NC * ((nu + KS_NC - 1) / KS_NC);
+          CHECK(KS_NXB >= NX && KS_NXB == KS_NR * KS_TR && KS_NXB == KS_NC * KS_TC, N, nu, T);
+          CHECK(KS_GS * N <= T && nup >= nu && KS_TR % 2 == 0, N, nu, T);
+          CHECK(Q.vp >= L.img && Q.end <= L.red, N, nu, T);
+          CHECK(Q.vp % 4 == 0 && Q.dx % 4 == 0 && Q.du % 4 == 0 && Q.bq % 4 == 0 && Q.th % 4 == 0, N, nu, T);
+          CHECK(Q.dx - Q.vp == N * KS_NXB && Q.du - Q.dx == N * KS_NXB, N, nu, T);
+          CHECK(Q.bq - Q.du >= N * nup && Q.th - Q.bq >= N * nup && Q.end - Q.th >= N, N, nu, T);
         }
         // the adjoint's scratch, appended after the solve layout
         if (T == 256) {

@@ -1,5 +1,5 @@
 """Host side of the launch-shape autotuner: the candidate list (the register
-PIPG form's thread rule and the shared-memory fit), the cache keys of both
+PIPG forms' thread rules and the shared-memory fit), the cache keys of both
 models, and the committed cache's entries."""
 import json
 
@@ -14,7 +14,13 @@ def test_register_form_thread_rule():
     assert A.reg_threads(15, 4, "3dof") == 128 + 64
 
 
-def test_candidates_fit_and_cover_both_forms():
+def test_tiled_form_thread_rule():
+    # 8 lanes per node (4 when NX <= 8) in whole warps
+    assert A.ks_threads(15) == 128 and A.ks_threads(30) == 256 and A.ks_threads(32) == 256
+    assert A.ks_threads(15, "3dof") == 64 and A.ks_threads(10, "3dof") == 64
+
+
+def test_candidates_fit_and_cover_every_form():
     c6 = A.candidates(15, 4, 0)
     assert (1, 128) in c6 and (1, 512) in c6 and (2, 288) in c6
     assert all(t % 32 == 0 and 128 <= t <= 576 for _, t in c6)
@@ -24,6 +30,8 @@ def test_candidates_fit_and_cover_both_forms():
     assert (2, 576) in A.candidates(15, 4, 1) and (2, 576) not in c6
     c3 = A.candidates(15, 4, 0, model="3dof")
     assert (1, 128) in c3 and (2, 192) in c3 and (2, 160) not in c3
+    assert (3, 128) in c6 and (3, 96) not in c6 and (3, 512) in c6 and (3, 544) not in c6
+    assert (3, 64) in c3
 
 
 def test_cache_keys_and_committed_entries():

@@ -74,11 +74,12 @@ def test_subproblem_blocks(torch_cuda, oracle, inputs, gs):
     S.close()
 
 
-@pytest.mark.parametrize("form,soc", [(1, 0), (2, 0), (1, 1), (2, 1)])
+@pytest.mark.parametrize("form,soc", [(1, 0), (2, 0), (1, 1), (2, 1), (3, 0), (3, 1)])
 def test_scp_step_forced_counts(torch_cuda, oracle, inputs, form, soc):
     """Three chained SCP iterations with the oracle's counts forced, PIPG in
-    shared memory (form 1) and in registers (form 2), with and without the
-    thrust-sector projection."""
+    shared memory (form 1), in registers (form 2) and in register tiles over
+    lane groups (form 3: four lanes per 8 x 8 block here), with and without
+    the thrust-sector projection."""
     torch = torch_cuda
     Ns = np.array([15, 10, 4, 15, 2], np.int32)
     p, S = _solver(inputs, 15, form=form, soc_thrust=soc)
@@ -136,7 +137,7 @@ def _solve_and_replay(torch, oracle, p, S, x0, Ns, mode, sample, converged_only=
     return o
 
 
-@pytest.mark.parametrize("mode,form", [(1, 0), (0, 0), (2, 0), (1, 2), (0, 2)])
+@pytest.mark.parametrize("mode,form", [(1, 0), (0, 0), (2, 0), (1, 2), (0, 2), (1, 3), (0, 3), (2, 3)])
 def test_full_solve_matches_oracle_replay(torch_cuda, oracle, inputs, mode, form):
     """Whole SCP solves on an uneven-N batch in every execution form and both
     PIPG layouts."""
@@ -177,12 +178,13 @@ def test_paper_distribution_sampled(torch_cuda, oracle, inputs):
     S.close()
 
 
-def test_fp32_tracks_fp64_oracle(torch_cuda, oracle, inputs):
-    """FP32 (register PIPG by default) against the FP64 oracle's free runs: on
-    the instances converged on both sides with equal SCP counts (at least 64
-    of 96), X, U, t_f and fuel within the FP32 tolerance."""
+@pytest.mark.parametrize("form", [0, 3])
+def test_fp32_tracks_fp64_oracle(torch_cuda, oracle, inputs, form):
+    """FP32 (form 0: the automatic PIPG form) against the FP64 oracle's free
+    runs: on the instances converged on both sides with equal SCP counts (at
+    least 64 of 96), X, U, t_f and fuel within the FP32 tolerance."""
     torch = torch_cuda
-    p, S32 = _solver(inputs, 15, precision=1)
+    p, S32 = _solver(inputs, 15, precision=1, form=form)
     B = 96
     x0 = inputs.dispersion(p, B, 9, "bj")
     o = {k: v.cpu().numpy() for k, v in S32.solve(_d(torch, x0), mode=1).items()}

@@ -36,13 +36,13 @@ def _fd(oracle, p, x0, X, U, ws, sig, n, h=1e-6):
                                         (4, 12, 3, {"glide_slope": 1, "dt_min": 0.3, "dt_max": 0.55}),
                                         (4, 15, 4, {"model": "3dof"}),
                                         (4, 11, 3, {"model": "3dof", "glide_slope": 1}),
-                                        (4, 10, 3, {"pipg_form": 2})])
+                                        (4, 10, 3, {"pipg_form": 2}), (4, 10, 3, {"pipg_form": 3})])
 def test_gradient_matches_oracle_finite_differences(torch_cuda, oracle, inputs, nu, N, B, ov):
     """Both models: the 6-DoF one of Sec. 4 and the 3-DoF instance of the
     template (gradient d L / d (m_wet, r, v) there).  With the shared-memory
     PIPG form the solve records the last PIPG loop's checkpoints for the
-    adjoint; with the register form (pipg_form 2) the adjoint reruns that
-    loop itself: both paths are checked."""
+    adjoint; with the register forms (pipg_form 2 and 3) the adjoint reruns
+    that loop itself: both paths are checked."""
     torch = torch_cuda
     from paper_2404_18034_gb300.pdg_mc import Solver
     ov = dict(ov)

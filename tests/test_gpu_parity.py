@@ -27,7 +27,8 @@ def torch_cuda():
 
 
 def _solver(inputs, nu=4, n_max=15, precision=0, form=0, **ov):
-    """form: PIPG layout (0 automatic, 1 shared memory, 2 registers)."""
+    """form: PIPG layout (0 automatic, 1 shared memory, 2 registers, 3 register
+    tiles over lane groups)."""
     from paper_2404_18034_gb300.pdg_mc import Solver
     p = inputs.load_params(nu=nu, **ov)
     S = Solver(p, n_max, precision)
@@ -75,11 +76,12 @@ def test_subproblem_blocks(torch_cuda, oracle, inputs, nu, prec):
         assert np.all(o["Am"][b, N - 1:].cpu().numpy() == 0)
 
 
-@pytest.mark.parametrize("nu,form", [(4, 1), (7, 1), (4, 2), (7, 2)])
+@pytest.mark.parametrize("nu,form", [(4, 1), (7, 1), (4, 2), (7, 2), (4, 3), (7, 3)])
 def test_scp_step_forced_counts(torch_cuda, oracle, inputs, nu, form):
     """Three chained SCP iterations (discretize, scale, power iteration, PIPG
     with the oracle's counts forced, update) match the oracle's iterations,
-    with the PIPG loop in shared memory (form 1) and in registers (form 2)."""
+    with the PIPG loop in shared memory (form 1), in registers (form 2) and in
+    register tiles over lane groups (form 3)."""
     torch = torch_cuda
     Ns = np.array([15, 10, 4, 15], np.int32)
     p, S = _solver(inputs, nu, 15, form=form)
@@ -160,24 +162,25 @@ def test_full_solve_matches_oracle_replay(torch_cuda, oracle, inputs, mode):
     assert np.mean(o["status"] == 0) >= 0.75  # the replayed sample above converges on both sides
 
 
-@pytest.mark.parametrize("mode", [1, 0, 2])
-def test_register_form_matches_oracle_replay(torch_cuda, oracle, inputs, mode):
-    """The register-resident PIPG form in FP64, whole solves on an uneven
-    batch (N in {10, 15, 20}; ragged rows and control lanes), every form of
-    execution, against the oracle replay at the FP64 tolerance."""
+@pytest.mark.parametrize("mode,form", [(1, 2), (0, 2), (2, 2), (1, 3), (0, 3), (2, 3)])
+def test_register_form_matches_oracle_replay(torch_cuda, oracle, inputs, mode, form):
+    """The register-resident PIPG forms in FP64, whole solves on an uneven
+    batch (N in {10, 15, 20}; ragged rows and control lanes; form 3 also a
+    half-used last warp at N = 15), every form of execution, against the
+    oracle replay at the FP64 tolerance."""
     torch = torch_cuda
-    p, S = _solver(inputs, 4, 20, form=2)
+    p, S = _solver(inputs, 4, 20, form=form)
     B = 9
     x0 = inputs.dispersion(p, B, 21, "bj")
     Ns = np.array([10, 15, 20] * 3, np.int32)
     o = _solve_and_replay(torch, oracle, inputs, p, S, x0, Ns, mode, range(B))
     assert np.mean(o["status"] == 0) >= 0.75
-    assert S.launch_info()["pipg_form"] == 2
+    assert S.launch_info()["pipg_form"] == form
 
 
 def test_pipg_form_selection(torch_cuda, inputs):
-    """Automatic choice (registers for FP32, shared memory for FP64), the
-    thread-count rule of the register form, and rejected settings."""
+    """Automatic choice (register tiles for FP32, shared memory for FP64), the
+    thread-count rules of the register forms, and rejected settings."""
     torch = torch_cuda
     p = inputs.load_params()
     from paper_2404_18034_gb300.pdg_mc import Solver
@@ -185,22 +188,34 @@ def test_pipg_form_selection(torch_cuda, inputs):
     S64, S32 = Solver(p, 15, 0), Solver(p, 15, 1)
     S64.solve(x0, mode=1); S32.solve(x0, mode=1)
     torch.cuda.synchronize()
-    assert S64.launch_info()["pipg_form"] == 1 and S32.launch_info()["pipg_form"] == 2
-    assert S32.launch_info()["threads"] == 224 + 64
-    S32.set_threads(160)            # below the register form's need: automatic falls back
+    assert S64.launch_info()["pipg_form"] == 1 and S32.launch_info()["pipg_form"] == 3
+    assert S32.launch_info()["threads"] == 128  # 8 lanes per node: 120 -> 128 threads at N = 15
+    S32.set_threads(96)             # below form 3's need: automatic falls back to form 1
     S32.solve(x0, mode=1)
     torch.cuda.synchronize()
     assert S32.launch_info()["pipg_form"] == 1
-    S32.set_pipg_form(2)            # ... and an explicit request is refused
+    S32.set_pipg_form(3)            # ... and an explicit request is refused
     with pytest.raises(RuntimeError, match="EINVAL"):
         S32.solve(x0, mode=1)
+    S32.set_pipg_form(2)            # form 2 needs 224 + 64 threads
+    S32.set_threads(256)
     with pytest.raises(RuntimeError, match="EINVAL"):
-        S64.set_pipg_form(3)
+        S32.solve(x0, mode=1)
+    S32.set_threads(0)
+    S32.solve(x0, mode=1)
+    torch.cuda.synchronize()
+    assert S32.launch_info()["pipg_form"] == 2 and S32.launch_info()["threads"] == 288
+    with pytest.raises(RuntimeError, match="EINVAL"):
+        S64.set_pipg_form(4)
     S64.set_pipg_form(2)
     S64b = Solver(p, 30, 0)
     S64b.set_pipg_form(2)           # FP64 register form: at most 512 threads (N = 30 needs 576)
     with pytest.raises(RuntimeError, match="EINVAL"):
         S64b.solve(torch.from_numpy(inputs.dispersion(p, 1, 3, "bj")).cuda(), mode=1)
+    S64b.set_pipg_form(3)           # form 3 at N = 30: 256 threads
+    S64b.solve(torch.from_numpy(inputs.dispersion(p, 1, 3, "bj")).cuda(), mode=1)
+    torch.cuda.synchronize()
+    assert S64b.launch_info()["pipg_form"] == 3 and S64b.launch_info()["threads"] == 256
 
 
 def test_fp32_register_form_tracks_shared_form(torch_cuda, oracle, inputs):
@@ -233,12 +248,12 @@ def test_nu7_solve_matches_oracle_replay(torch_cuda, oracle, inputs):
     _solve_and_replay(torch, oracle, inputs, p, S, x0, None, 1, range(4))
 
 
-@pytest.mark.parametrize("mode,form", [(1, 1), (0, 1), (1, 2), (2, 1)])
+@pytest.mark.parametrize("mode,form", [(1, 1), (0, 1), (1, 2), (2, 1), (1, 3), (0, 3)])
 def test_pipg_stop_decisions_match_oracle(torch_cuda, oracle, inputs, mode, form):
     """PIPG tolerance 1e-4 at N = 10: most subproblems stop on Alg. stopping
     before the iteration cap (at the default 1e-6 nearly all run to the cap),
     so the PIPG stop decisions are exercised.  Whole solves in every
-    execution form and both PIPG layouts; every power, PIPG and SCP decision
+    execution form and every PIPG layout; every power, PIPG and SCP decision
     of the converged instances agrees with the oracle's own test on the
     replayed iterates, and at least 40 PIPG loops stopped on their test."""
     torch = torch_cuda
@@ -252,8 +267,8 @@ def test_pipg_stop_decisions_match_oracle(torch_cuda, oracle, inputs, mode, form
     assert early >= 40, early
 
 
-@pytest.mark.parametrize("eps_rel", [1e-6, 1e-4])
-def test_free_run_agrees_with_oracle(torch_cuda, oracle, inputs, eps_rel):
+@pytest.mark.parametrize("eps_rel,form", [(1e-6, 0), (1e-4, 0), (1e-4, 3)])
+def test_free_run_agrees_with_oracle(torch_cuda, oracle, inputs, eps_rel, form):
     """Without replay both sides take their own stop decisions.  With every
     decision equal (the stop-decision check above), the free runs must match
     count for count: every instance's status, SCP count and per-iteration
@@ -261,7 +276,7 @@ def test_free_run_agrees_with_oracle(torch_cuda, oracle, inputs, eps_rel):
     converged ones.  A decision may differ only where the oracle's own margin
     is borderline; such instances are counted and must be rare."""
     torch = torch_cuda
-    p, S = _solver(inputs, 4, 10, pipg_eps_rel=eps_rel)
+    p, S = _solver(inputs, 4, 10, form=form, pipg_eps_rel=eps_rel)
     B = 48
     x0 = inputs.dispersion(p, B, inputs.config_seed(1), "bj")
     out = S.solve(torch.from_numpy(x0).cuda(), mode=1, trace=True)
@@ -373,14 +388,14 @@ def test_plain_and_persistent_agree(torch_cuda, inputs):
         assert_scaled_close(c["U"][i].cpu().numpy(), b["U"][i].cpu().numpy(), p["P_u"][:4], what=f"classed U {i}")
 
 
-@pytest.mark.parametrize("N,prec", [(15, 1), (30, 1)])
-def test_fp32_build_tracks_fp64_oracle(torch_cuda, oracle, inputs, N, prec):
+@pytest.mark.parametrize("N,prec,form", [(15, 1, 0), (30, 1, 0), (15, 1, 3), (30, 1, 3)])
+def test_fp32_build_tracks_fp64_oracle(torch_cuda, oracle, inputs, N, prec, form):
     """The FP32 build against the FP64 oracle's free runs: on the instances
     that converge on both sides in the same number of SCP iterations (at
     least 64 of 96), the scaled X and U errors and the relative t_f and fuel
-    errors are within the FP32 tolerance."""
+    errors are within the FP32 tolerance.  Form 0 is the automatic choice."""
     torch = torch_cuda
-    p, S = _solver(inputs, 4, N, precision=prec)
+    p, S = _solver(inputs, 4, N, precision=prec, form=form)
     B = 96
     x0 = inputs.dispersion(p, B, inputs.config_seed(3 if N == 15 else 5), "bj")
     out = S.solve(torch.from_numpy(x0).cuda(), mode=1)
@@ -389,7 +404,7 @@ def test_fp32_build_tracks_fp64_oracle(torch_cuda, oracle, inputs, N, prec):
     ref = oracle.solve_batch(p, x0, np.full(B, N, np.int32))
     both = np.nonzero((o["status"] == 0) & (ref["status"] == 0) & (o["scp_iters"] == ref["scp_iters"]))[0]
     e = fp32_errors(p, o, ref, both)
-    print(f"FP32 N={N}: {len(both)} of {B} comparable; errors {e}; converged FP32 {np.mean(o['status'] == 0):.3f}")
+    print(f"FP32 N={N} form {form}: {len(both)} of {B} comparable; errors {e}; converged FP32 {np.mean(o['status'] == 0):.3f}")
     assert len(both) >= 64
     for k, v in e.items():
         assert v <= FP32_TOL, (k, v)
@@ -479,7 +494,7 @@ def test_budget_status(torch_cuda, inputs):
     assert np.all(out["status"].cpu().numpy() == PDG_BUDGET)
 
 
-@pytest.mark.parametrize("nu,form", [(4, 1), (7, 1), (4, 2)])
+@pytest.mark.parametrize("nu,form", [(4, 1), (7, 1), (4, 2), (4, 3), (7, 3)])
 def test_soc_variant_matches_oracle(torch_cuda, oracle, inputs, nu, form):
     """soc_thrust = 1 (thrust sector by projection inside PIPG): chained SCP
     steps with forced counts and full solves match the oracle replay."""
@@ -539,10 +554,10 @@ def test_subproblem_blocks_with_glide_slope(torch_cuda, oracle, inputs, nu):
     assert active >= 10
 
 
-@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("form", [1, 2, 3])
 def test_glide_slope_and_time_bounds_match_oracle(torch_cuda, oracle, inputs, form):
     """Glide-slope row and the time-bound box: chained SCP steps with forced
-    counts, then full solves against the oracle replay, in both PIPG forms."""
+    counts, then full solves against the oracle replay, in every PIPG form."""
     torch = torch_cuda
     ov = dict(glide_slope=1, dt_min=0.3, dt_max=0.5, tf_max=6.6)
     p, S = _solver(inputs, 4, 15, form=form, **ov)
