@@ -54,6 +54,21 @@ using namespace pdg;
 #ifndef PDG_FP64_MINB
 #define PDG_FP64_MINB 1
 #endif
+// The persistent kernel of form 3 (FP32) is built for at most
+// PDG_KS_PERS_MAXT threads (N <= 32 needs 256), so that it may take 65536 /
+// PDG_KS_PERS_MAXT registers (168 for 384 threads: three CTAs per SM at N =
+// 15; at 128 registers its PIPG loop reloads its tiles from local memory).  It also inlines the discretization (PDG_KS_DISC_INLINE):
+// an out-of-line call costs its PIPG loop registers.
+#ifndef PDG_KS_DISC_INLINE
+#define PDG_KS_DISC_INLINE 1
+#endif
+#ifndef PDG_KS_PERS_MAXT
+#define PDG_KS_PERS_MAXT 384
+#endif
+#define PDG_LB_PERS(R, PV)                                                                  \
+  __launch_bounds__((PV) == 3 && sizeof(R) == 4 ? PDG_KS_PERS_MAXT                            \
+                    : ((PV) == 2 && sizeof(R) == 4 ? PDG_REG_MAXT_F32 : (sizeof(R) == 8 ? PDG_FP64_MAXT : 512)), \
+                    sizeof(R) == 8 ? PDG_FP64_MINB : ((PV) == 1 ? PDG_FP32_MIN_BLOCKS : 1))
 #define PDG_LB(R, PV)                                                                       \
   __launch_bounds__((PV) == 2 && sizeof(R) == 4 ? PDG_REG_MAXT_F32 : (sizeof(R) == 8 ? PDG_FP64_MAXT : 512), \
                     sizeof(R) == 8 ? PDG_FP64_MINB : ((PV) == 1 ? PDG_FP32_MIN_BLOCKS : 1))
@@ -134,7 +149,7 @@ __device__ void write_outputs(const Lay& L, const R* sm, int b, int Nmax, int st
 // rerun the last PIPG loop forward.  Record of an instance (offsets for its N):
 // X_bar, U_bar | warm start | sigma, PIPG count | x_hat, u_hat | checkpoints.
 template <typename R, int NU, int PV, bool CK = false>
-__global__ void PDG_LB(R, PV)
+__global__ void PDG_LB_PERS(R, PV)
 k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, const int* __restrict__ Ns,
              double* X, double* U, double* tf, double* fuel, int* status, int* scp_iters, long long* pipg_iters,
              int* trace, int* queue, double* rec, int rec_stride, const int* perm, const int* class_off, int cls) {
@@ -205,7 +220,9 @@ k_persistent(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
         for (int t = threadIdx.x; t < nw; t += blockDim.x) rc[ow + t] = double(sm[L.xh + t]);
       }
       {
-        const R defect = phase_discretize<R, NU>(P, L, sm);
+        R defect;
+        if constexpr (PV == 3 && PDG_KS_DISC_INLINE) defect = discretize_body<R, NU>(P, L, sm);
+        else defect = phase_discretize<R, NU>(P, L, sm);
         if (threadIdx.x == 0) C.defect = double(defect);
       }
       phase_scale_extra<R, NU>(P, L, sm);
@@ -934,7 +951,7 @@ static bool plan_for(const pdg_handle* h, int N, Plan* out, std::string* why, bo
   const int ov = use_override ? h->threads_override : 0;
   const int tks = pipg_ks_threads(N);
   int pv = h->pipg_variant;
-  if (pv == 0) pv = (h->p.precision == 1 && tks <= 512 && (ov == 0 || (ov >= tks && ov <= 512))) ? 3 : 1;
+  if (pv == 0) pv = (h->p.precision == 1 && (ov == 0 || (ov >= tks && ov <= PDG_KS_PERS_MAXT))) ? 3 : 1;
   if (pv == 2) {
     const int T = ov > 0 ? ov : treg;
     if (T < treg || T > maxt) {
@@ -947,8 +964,10 @@ static bool plan_for(const pdg_handle* h, int N, Plan* out, std::string* why, bo
     // the lane groups' threads, at least two warps (the discretization wants
     // one interval per wave); the plain form's other kernels at least 128
     const int T = ov > 0 ? ov : (tks < 64 ? 64 : tks);
-    if (T < tks || T > 512) {
-      *why = "PIPG form 3 needs " + std::to_string(tks) + " to 512 threads per CTA at N = " + std::to_string(N);
+    const int tmax = h->p.precision == 1 ? PDG_KS_PERS_MAXT : 512;
+    if (T < tks || T > tmax) {
+      *why = "PIPG form 3 needs " + std::to_string(tks) + " to " + std::to_string(tmax) +
+             " threads per CTA at N = " + std::to_string(N);
       return false;
     }
     *out = {T, T < 128 ? 128 : T, 3};
@@ -1615,7 +1634,8 @@ int pdg_mc_autotune(pdg_handle* h, int B, const double* x0, const int* n_nodes, 
   // candidates: (form 1, 128..512), (form 2, its minimum .. its limit) and
   // (form 3, its minimum .. 512), multiples of 32
   for (int form = 1; form <= 3 && rc == PDG_OK; ++form) {
-    const int t_lo = form == 1 ? 128 : (form == 2 ? treg : tks), t_hi = form == 2 ? maxt : 512;
+    const int t_lo = form == 1 ? 128 : (form == 2 ? treg : tks);
+    const int t_hi = form == 2 ? maxt : (form == 3 && h->p.precision == 1 ? PDG_KS_PERS_MAXT : 512);
     for (int T = t_lo; T <= t_hi && rc == PDG_OK; T += 32) {
       h->pipg_variant = form;
       h->threads_override = T;

@@ -34,7 +34,7 @@ __device__ void phase_init_guess(const DParams& P, const Lay& L, R* sm) {
 #define PDG_DISC_ATTR __noinline__
 #endif
 template <typename R, int NU>
-__device__ PDG_DISC_ATTR R phase_discretize(const DParams& P, const Lay& L, R* sm) {
+__device__ __forceinline__ R discretize_body(const DParams& P, const Lay& L, R* sm) {
   constexpr int NCOL = NX + 2 * NU;
   const int N = L.N;
   const R* Xb = sm + L.Xb;
@@ -141,6 +141,13 @@ __device__ PDG_DISC_ATTR R phase_discretize(const DParams& P, const Lay& L, R* s
   R v[1] = {dmax};
   block_max_k<R, 1>(v, sm + L.red);
   return v[0];
+}
+// Out of line by default (one copy serves every kernel).  The persistent
+// kernel of PIPG form 3 inlines the body instead: a call in that kernel
+// leaves its PIPG loop fewer registers for its tiles.
+template <typename R, int NU>
+__device__ PDG_DISC_ATTR R phase_discretize(const DParams& P, const Lay& L, R* sm) {
+  return discretize_body<R, NU>(P, L, sm);
 }
 
 // Sec. 2.3.2: hat eps_k, the dilation box, hat z_i (every component of
@@ -1078,6 +1085,8 @@ __device__ __forceinline__ R ks_all_sum(R x) {
   return x;
 }
 
+template <int V> struct KsTag { static constexpr int value = V; };
+
 #ifdef PDG_PIPG_KS_NOINLINE
 #define PDG_PKS_ATTR __noinline__
 #else
@@ -1149,16 +1158,21 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
   // ---- iterates.  x components TC cb + WC rb + e of node g, dual rows
   // TR rb + WR cb + e of interval g, controls cb + NCB s of node g (on every
   // lane of the tile column)
-  R xt[WC], xh[WC], zfx[WC], dxn[WC];
+  // Only the relaxed iterates stay in registers.  The unextrapolated ones
+  // (x_hat, u_hat, mu+-, phi, theta) are what the stop test compares and what
+  // the loop returns: the iteration before a tested one and the tested one
+  // write them to the image, where the tested one reads them back, and the
+  // last iteration leaves them there.
+  R xt[WC], zfx[WC], dxn[WC];
   bool fx[WC], okx[WC], okd[WR];
-  R nvp[WR], nvm[WR], mup[WR], mum[WR], ft[WR], fh[WR], wv[WR];
-  R ut[NC], uh[NC], tref[NC], dun[NC];
+  R nvp[WR], nvm[WR], ft[WR], wv[WR];
+  R ut[NC], dun[NC];
   T2 fg[TH];
 #pragma unroll
   for (int e = 0; e < WC; ++e) {
     const int c = TC * cb + WC * rb + e;
     okx[e] = live && c < NX;
-    xt[e] = xh[e] = okx[e] ? sm[L.xh + g * NX + c] : R(0);
+    xt[e] = okx[e] ? sm[L.xh + g * NX + c] : R(0);
     fx[e] = okx[e] && (g == 0 || (g == N - 1 && P.fix_f[c]));
     zfx[e] = !okx[e] ? R(0) : (g == 0 ? sm[L.zi + c] : (fx[e] ? sm[L.zf + c] : R(0)));
     dxn[e] = 0;
@@ -1169,11 +1183,9 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
     okd[e] = has_iv && i < NX;
     const int o = g * NX + i;
     wv[e] = okd[e] ? sm[L.w + o] : R(0);
-    mup[e] = okd[e] ? sm[L.mup + o] : R(0);
-    mum[e] = okd[e] ? sm[L.mum + o] : R(0);
-    nvp[e] = okd[e] ? mup[e] - aw : R(0);
-    nvm[e] = okd[e] ? mum[e] - aw : R(0);
-    ft[e] = fh[e] = okd[e] ? sm[L.phi + o] : R(0);
+    nvp[e] = okd[e] ? sm[L.mup + o] - aw : R(0);
+    nvm[e] = okd[e] ? sm[L.mum + o] - aw : R(0);
+    ft[e] = okd[e] ? sm[L.phi + o] : R(0);
   }
 #pragma unroll
   for (int h = 0; h < TH; ++h) {
@@ -1185,16 +1197,15 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
   for (int s = 0; s < NC; ++s) {
     const int cc = cb + NCB * s;
     const bool ok = live && cc < NU;
-    ut[s] = uh[s] = ok ? sm[L.uh + g * NU + cc] : R(0);
-    tref[s] = (ok && cc < 3) ? sm[L.Ub + g * NU + cc] : R(0);
+    ut[s] = ok ? sm[L.uh + g * NU + cc] : R(0);
     dun[s] = 0;
   }
   const R lo = sm[L.lo + gv], hi = sm[L.hi + gv];
   // the lane that owns dual row IY of interval g also owns theta_g
   const int iy0 = TR * rb + WR * cb;
   const bool th_lane = has_iv && IY >= iy0 && IY < iy0 + WR;
-  R tht = 0, thh = 0, eps = 0;
-  if (th_lane) { tht = thh = sm[L.th + g]; eps = sm[L.eps + g]; }
+  R tht = 0;
+  if (th_lane) tht = sm[L.th + g];
   __syncthreads();  // the exchange region is zero
 #pragma unroll
   for (int e = 0; e < WR; ++e)
@@ -1213,12 +1224,14 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
   };
   if (wlive) bq_out();
   __syncthreads();
-  const R sa = R(P.soc_tan), tmax = R(P.T_max), pT = R(P.Pu[0]), ipT = R(P.Puinv[0]);
   const R acost = alpha * R(P.w_cost);
   const int jmax = force > 0 ? force : P.pipg_jmax;
   const int jcheck = P.pipg_jcheck;
-  auto iterate = [&](auto chk_tag) -> bool {
-    constexpr bool chk = decltype(chk_tag)::value;
+  // V = 0: plain iteration; 1: also stores the unextrapolated iterates in
+  // the image; 2: runs the stop test against the stored ones, then stores
+  auto iterate = [&](auto v_tag) -> bool {
+    constexpr int V = decltype(v_tag)::value;
+    constexpr bool chk = V == 2, st = V >= 1;
     U zn = 0, zo = 0, zd = 0, rn = 0, ro = 0, rd = 0;
     // ---- projected gradient step (primal)
     if (wlive) {
@@ -1251,9 +1264,14 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
         if (okx[e]) dxs[g * NXB + c] = dxn[e];
         xt[e] += rho * (xn - xt[e]);
         if constexpr (chk) {
-          if (okx[e]) { zn = umax(zn, OB::abs(xn)); zo = umax(zo, OB::abs(xh[e])); zd = umax(zd, OB::abs(xn - xh[e])); }
+          if (okx[e]) {
+            const R old = sm[L.xh + g * NX + c];
+            zn = umax(zn, OB::abs(xn)); zo = umax(zo, OB::abs(old)); zd = umax(zd, OB::abs(xn - old));
+          }
         }
-        xh[e] = xn;
+        if constexpr (st) {
+          if (okx[e]) sm[L.xh + g * NX + c] = xn;
+        }
       }
       R un[NC];
 #pragma unroll
@@ -1266,10 +1284,17 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
         // the node's thrust onto the sector (cone about body x, then the
         // ball); component cc sits on lane cc % NCB of this tile row, in
         // control column cc / NCB, and every tile row projects alike
+        // (constants and the reference thrust read here: they would hold
+        // registers across the whole loop)
+        const R sa = R(P.soc_tan), tmax = R(P.T_max), pT = R(P.Pu[0]), ipT = R(P.Puinv[0]);
         const int base = (tid & 31) & ~(NCB - 1);
-        R tv[NC];
+        R tv[NC], tref[NC];
 #pragma unroll
-        for (int s = 0; s < NC; ++s) tv[s] = (cb + NCB * s < 3) ? tref[s] + pT * un[s] : R(0);
+        for (int s = 0; s < NC; ++s) {
+          const int cc = cb + NCB * s;
+          tref[s] = (live && cc < 3) ? sm[L.Ub + g * NU + cc] : R(0);
+          tv[s] = cc < 3 ? tref[s] + pT * un[s] : R(0);
+        }
         R T0 = __shfl_sync(0xffffffffu, tv[0], base);
         R T1 = __shfl_sync(0xffffffffu, tv[1 / NCB], base + 1 % NCB);
         R T2v = __shfl_sync(0xffffffffu, tv[2 / NCB], base + 2 % NCB);
@@ -1299,9 +1324,14 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
         if (ok && rb == 0) dus[g * NUP + cc] = dun[s];
         ut[s] += rho * (un[s] - ut[s]);
         if constexpr (chk) {
-          if (ok) { zn = umax(zn, OB::abs(un[s])); zo = umax(zo, OB::abs(uh[s])); zd = umax(zd, OB::abs(un[s] - uh[s])); }
+          if (ok) {
+            const R old = sm[L.uh + g * NU + cc];
+            zn = umax(zn, OB::abs(un[s])); zo = umax(zo, OB::abs(old)); zd = umax(zd, OB::abs(un[s] - old));
+          }
         }
-        uh[s] = un[s];
+        if constexpr (st) {
+          if (ok && rb == 0) sm[L.uh + g * NU + cc] = un[s];
+        }
       }
     }
     __syncthreads();
@@ -1336,23 +1366,31 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
         const R mm = max0(vb + alpha * f);
         nvp[e] = omr * va + (rho * mp - raw);
         nvm[e] = omr * vb + (rho * mm - raw);
+        const int o = g * NX + i;
         if constexpr (chk) {
           if (okd[e]) {
+            const R op = sm[L.mup + o], om = sm[L.mum + o];
             zn = umax(zn, umax(OB::nonneg(mp), OB::nonneg(mm)));
-            zo = umax(zo, umax(OB::nonneg(mup[e]), OB::nonneg(mum[e])));
-            zd = umax(zd, umax(OB::abs(mp - mup[e]), OB::abs(mm - mum[e])));
+            zo = umax(zo, umax(OB::nonneg(op), OB::nonneg(om)));
+            zd = umax(zd, umax(OB::abs(mp - op), OB::abs(mm - om)));
           }
         }
-        mup[e] = mp;
-        mum[e] = mm;
+        if constexpr (st) {
+          if (okd[e]) { sm[L.mup + o] = mp; sm[L.mum + o] = mm; }
+        }
         const R r0 = wv[e] + (fma(R(2), mp, -va) - fma(R(2), mm, -vb)) - dxs[gp1 * NXB + i] + rs[e];
         const R r = okd[e] ? r0 : R(0);  // rows that do not exist keep phi~ = 0
         const R pn = f + beta * r;
         ft[e] = f + rhb * r;  // = phi~ + rho (phi_new - phi~)
         if constexpr (chk) {
-          if (okd[e]) { rn = umax(rn, OB::abs(pn)); ro = umax(ro, OB::abs(fh[e])); rd = umax(rd, OB::abs(pn - fh[e])); }
+          if (okd[e]) {
+            const R old = sm[L.phi + o];
+            rn = umax(rn, OB::abs(pn)); ro = umax(ro, OB::abs(old)); rd = umax(rd, OB::abs(pn - old));
+          }
         }
-        fh[e] = pn;
+        if constexpr (st) {
+          if (okd[e]) sm[L.phi + o] = pn;
+        }
         if (okd[e]) vps[g * NXB + i] = ft[e];
       }
       {
@@ -1363,11 +1401,14 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
       }
       bq_out();
       if (th_lane) {
-        const R hy = dxs[gp1 * NXB + IY] - dxs[g * NXB + IY] - eps;
+        const R hy = dxs[gp1 * NXB + IY] - dxs[g * NXB + IY] - sm[L.eps + g];
         const R tn = max0(tht + beta * hy);
         tht += rho * (tn - tht);
-        if constexpr (chk) { rn = umax(rn, OB::nonneg(tn)); ro = umax(ro, OB::abs(thh)); rd = umax(rd, OB::abs(tn - thh)); }
-        thh = tn;
+        if constexpr (chk) {
+          const R old = sm[L.th + g];
+          rn = umax(rn, OB::nonneg(tn)); ro = umax(ro, OB::abs(old)); rd = umax(rd, OB::abs(tn - old));
+        }
+        if constexpr (st) sm[L.th + g] = tn;
         ths[g] = tht;
       }
     }
@@ -1383,41 +1424,20 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
       return false;
     }
   };
-  // blocks of jcheck iterations whose last one runs the stop test, so that
-  // the loop carries no per-iteration remainder
+  // blocks of jcheck iterations whose last one runs the stop test (the one
+  // before it stores the iterates it compares with), so that the loop carries
+  // no per-iteration remainder; the last iteration of the loop stores
   const bool chk_on = force <= 0 && jcheck > 0;
   const int per = chk_on ? jcheck : (jmax > 0 ? jmax : 1);
   int j = 0;
   while (j < jmax) {
     const int nb = per < jmax - j ? per : jmax - j;
-    for (int k = 1; k < nb; ++k) iterate(ChkTag<false>{});
+    const bool tested = chk_on && nb == per;
+    const int plain = tested ? nb - 2 : nb - 1;
+    for (int k = 0; k < plain; ++k) iterate(KsTag<0>{});
+    if (!tested || nb >= 2) iterate(KsTag<1>{});
     j += nb;
-    if (chk_on && nb == per) {
-      if (iterate(ChkTag<true>{})) break;
-    } else {
-      iterate(ChkTag<false>{});
-    }
-  }
-  // iterates back to the image (warm start of the next SCP iteration)
-  if (wlive) {
-#pragma unroll
-    for (int e = 0; e < WC; ++e)
-      if (okx[e]) sm[L.xh + g * NX + TC * cb + WC * rb + e] = xh[e];
-#pragma unroll
-    for (int e = 0; e < WR; ++e) {
-      const int i = TR * rb + WR * cb + e;
-      if (okd[e]) {
-        sm[L.mup + g * NX + i] = mup[e];
-        sm[L.mum + g * NX + i] = mum[e];
-        sm[L.phi + g * NX + i] = fh[e];
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < NC; ++s) {
-      const int cc = cb + NCB * s;
-      if (live && cc < NU && rb == 0) sm[L.uh + g * NU + cc] = uh[s];
-    }
-    if (th_lane) sm[L.th + g] = thh;
+    if (tested && iterate(KsTag<2>{})) break;
   }
   __syncthreads();
   return j;
