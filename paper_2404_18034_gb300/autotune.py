@@ -26,6 +26,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "autotune_cache.json")
 NXS = {"6dof": 15, "3dof": 8}
+NNZA = {"6dof": 110, "3dof": 24}  # structural nonzeros of the interval STM
 SMEM_MAX = 232448
 
 
@@ -93,9 +94,10 @@ def _fitting(ts: Iterable[int], n_max: int, nu: int, precision: int, model: str 
         if ipw < 1:
             continue
         n = n_max
-        img = 8 + 16 + n * NX + n * nu + (n - 1) * (NX * NX + 2 * NX * nu + NX + 1) + 2 * n + 2 * NX + \
+        sas = (NNZA[model] + 1) | 1  # compact hat A^-: nonzeros, a zero, odd count
+        img = 8 + 16 + n * NX + n * nu + (n - 1) * (sas + 2 * NX * nu + NX + 1) + 2 * n + 2 * NX + \
             n * NX + n * nu + 3 * (n - 1) * NX + (n - 1)
-        uni = max(2 * n * NX + 2 * n * nu + 4 * (n - 1) * NX + (n - 1), ipw * (sa + NX * nu + 3 * NX))
+        uni = max(2 * n * NX + 2 * n * nu + 4 * (n - 1) * NX + (n - 1), ipw * (2 * (sa + NX * nu) + 3 * NX))
         if (img + uni + 210) * esz > SMEM_MAX:
             continue
         yield t

@@ -135,13 +135,13 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
         const double tdk = vth[k - 1] - (last ? 0.0 : vth[k]);
         const double G0 = fma(i == IY ? 1.0 : 0.0, tdk, -vph[(k - 1) * NX + i]);
         double Gc = G0;
-        const double* a = Am + km * NX * NX + i;
+        const double* a = Am + km * STM_SAS;
         const double* f = vph + km * NX;
         const int nj = kStm.col_nnz[kStm.col_order[(t & ~31) / (N - 1)]];
-        const unsigned long long lst = kStm.col_list[i];
+        const unsigned long long lst = kStm.col_list[i], w0 = kStm.col_off[i][0], w1 = kStm.col_off[i][1];
         for (int j = 0; j < nj; ++j) {
           const int r = int(lst >> (4 * j)) & 15;
-          Gc = fma(a[r * NX], f[r], Gc);
+          Gc = fma(a[stm_off(w0, w1, j)], f[r], Gc);
         }
         const double G = last ? G0 : Gc;
         const double cost = (last && i == IM) ? acost : 0.0;
@@ -205,10 +205,10 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
         sm[A.mum_m + o] = mb ? 1.0 : 0.0;
         double r = sm[L.w + o] + (fma(2.0, mp, -a) - fma(2.0, mm, -b)) - dx[(k + 1) * NX + i];
         const int nj = kStm.row_nnz[kStm.row_order[(t & ~31) / (N - 1)]];
-        const unsigned long long lst = kStm.row_list[i];
+        const unsigned long long lst = kStm.row_list[i], w0 = kStm.row_off[i][0], w1 = kStm.row_off[i][1];
         for (int j = 0; j < nj; ++j) {
           const int c = int(lst >> (4 * j)) & 15;
-          r = fma(Am[o * NX + c], dx[k * NX + c], r);
+          r = fma(Am[k * STM_SAS + stm_off(w0, w1, j)], dx[k * NX + c], r);
         }
         for (int c = 0; c < NU; ++c)
           r = fma(Bp[o * NU + c], du[(k + 1) * NU + c], fma(Bm[o * NU + c], du[k * NU + c], r));
@@ -316,13 +316,13 @@ __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& 
         const bool hasA = k < N - 1, hasP = k > 0;
         const int ka = hasA ? k : 0, kp = hasP ? k - 1 : 0;
         double dA = 0;
-        const double* a = Am + ka * NX * NX + i;
+        const double* a = Am + ka * STM_SAS;
         const double* f = rb + ka * NX;
         const int nj = kStm.col_nnz[kStm.col_order[(t & ~31) / N]];
-        const unsigned long long lst = kStm.col_list[i];
+        const unsigned long long lst = kStm.col_list[i], w0 = kStm.col_off[i][0], w1 = kStm.col_off[i][1];
         for (int j = 0; j < nj; ++j) {
           const int r = int(lst >> (4 * j)) & 15;
-          dA = fma(a[r * NX], f[r], dA);
+          dA = fma(a[stm_off(w0, w1, j)], f[r], dA);
         }
         const double hd = (hasP ? hb[kp] : 0.0) - (hasA ? hb[ka] : 0.0);
         double d = fma(i == IY ? 1.0 : 0.0, hd, hasA ? dA : 0.0);
@@ -366,10 +366,10 @@ __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& 
         double fb = vphb[o];
         double fa = fb;
         const int nj = kStm.row_nnz[kStm.row_order[(t & ~31) / (N - 1)]];
-        const unsigned long long lst = kStm.row_list[i];
+        const unsigned long long lst = kStm.row_list[i], w0 = kStm.row_off[i][0], w1 = kStm.row_off[i][1];
         for (int j = 0; j < nj; ++j) {
           const int c = int(lst >> (4 * j)) & 15;
-          fa = fma(Am[(kk * NX + i) * NX + c], Gb[kk * NX + c], fa);
+          fa = fma(Am[kk * STM_SAS + stm_off(w0, w1, j)], Gb[kk * NX + c], fa);
         }
         fb = k >= 1 ? fa : fb;
         fb -= Gb[(k + 1) * NX + i];

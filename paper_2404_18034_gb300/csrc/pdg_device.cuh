@@ -114,10 +114,21 @@ __host__ __device__ constexpr unsigned model_stm_row_mask(int) { return (1u << N
 // the most (the warp runs that many, on the GB300 FP64 pipe each costs a full
 // warp instruction).  A task with fewer entries than its warp's first pads its
 // index list with one of its own structural zeros, which adds exactly nothing.
+//
+// The blocks hold only the structural nonzeros (compact storage): interval k
+// keeps its nonzeros row by row, columns ascending, at k * STM_SAS, then one
+// zero (offset nnz) and padding to an odd count.  row_off[i] / col_off[i]
+// give, in the order of row_list[i] / col_list[i], each entry's offset within
+// the interval's block as 8-bit fields (entries 0..7 in word 0, 8..14 in word
+// 1); a padding entry points at the zero.
 struct StmOrder {
   unsigned char row_order[NXMAX], col_order[NXMAX];  // rows / columns, most nonzeros first
   unsigned char row_nnz[NXMAX], col_nnz[NXMAX];
   unsigned long long row_list[NXMAX], col_list[NXMAX];  // 4-bit indices, ascending, then padding
+  unsigned long long row_off[NXMAX][2], col_off[NXMAX][2];
+  unsigned row_mask[NXMAX];
+  unsigned char row_start[NXMAX];  // offset of row i's first nonzero
+  int nnz;
 };
 
 __host__ __device__ constexpr bool stm_nz(int i, int c) { return (model_stm_row_mask(i) >> c) & 1u; }
@@ -137,6 +148,27 @@ __host__ __device__ constexpr StmOrder make_stm_order() {
     S.col_nnz[i] = (unsigned char)nc;
     S.row_list[i] = lr;
     S.col_list[i] = lc;
+    S.row_mask[i] = model_stm_row_mask(i) & ((1u << NX) - 1u);
+    S.row_start[i] = (unsigned char)S.nnz;
+    S.nnz += nr;
+  }
+  // offsets of the list entries: (r, c) sits at row_start[r] + (nonzeros of
+  // row r left of column c); padding entries at the zero (offset nnz)
+  for (int i = 0; i < NX; ++i) {
+    for (int j = 0; j < NX; ++j) {
+      const int c = int(S.row_list[i] >> (4 * j)) & 15, r = int(S.col_list[i] >> (4 * j)) & 15;
+      int oc = S.nnz, orr = S.nnz;
+      if (j < S.row_nnz[i]) {
+        oc = S.row_start[i];
+        for (int q = 0; q < c; ++q) oc += stm_nz(i, q) ? 1 : 0;
+      }
+      if (j < S.col_nnz[i]) {
+        orr = S.row_start[r];
+        for (int q = 0; q < i; ++q) orr += stm_nz(r, q) ? 1 : 0;
+      }
+      S.row_off[i][j >> 3] |= (unsigned long long)oc << (8 * (j & 7));
+      S.col_off[i][j >> 3] |= (unsigned long long)orr << (8 * (j & 7));
+    }
   }
   for (int a = 0; a < NX; ++a) { S.row_order[a] = (unsigned char)a; S.col_order[a] = (unsigned char)a; }
   for (int a = 1; a < NX; ++a)  // stable insertion sort, most nonzeros first
@@ -152,8 +184,24 @@ __host__ __device__ constexpr StmOrder make_stm_order() {
 }
 static __constant__ StmOrder kStm = make_stm_order();
 
-// stage buffer of one interval: compact A (SA_A), dense B (NX x nu), then the
-// evaluator's RK4 state of x: base P, accumulator, stage input (NX each)
+// compact block stride per interval: the nonzeros, the zero, and an odd
+// count, so that the same entry of consecutive intervals (the tasks of a
+// warp) falls in different shared-memory banks
+constexpr int STM_SAS = (make_stm_order().nnz + 1) | 1;
+
+// offset of entry j of a row or column list (w = kStm.row_off[i] or col_off[i])
+__device__ __forceinline__ int stm_off(unsigned long long w0, unsigned long long w1, int j) {
+  return int((j < 8 ? w0 : w1) >> (8 * (j & 7))) & 255;
+}
+// offset of (r, c) in an interval's compact block (the zero for a structural zero)
+__device__ __forceinline__ int stm_index(int r, int c) {
+  const unsigned m = kStm.row_mask[r];
+  return ((m >> c) & 1u) ? int(kStm.row_start[r]) + __popc(m & ((1u << c) - 1u)) : kStm.nnz;
+}
+
+// stage buffer of one interval: two Jacobian buffers, each compact A (SA_A)
+// and dense B (NX x nu), then the evaluator's RK4 state of x: base P,
+// accumulator, stage input (NX each)
 
 // Intervals per discretization wave: warp 0 evaluates the model of up to 32
 // intervals, the remaining warps hold one STM column per thread.
@@ -170,13 +218,13 @@ __host__ __device__ inline Lay make_lay(int N, int nu, int threads) {
   L.N = N;
   L.nu = nu;
   L.ipw = waves_ipw(threads, nu);
-  L.sa = SA_A + NX * nu + 3 * NX;
+  L.sa = 2 * (SA_A + NX * nu) + 3 * NX;
   int o = 0;
   L.sc = o; o += 8;
   L.x0 = o; o += 16;
   L.Xb = o; o += N * NX;
   L.Ub = o; o += N * nu;
-  L.Am = o; o += (N - 1) * NX * NX;
+  L.Am = o; o += (N - 1) * STM_SAS;  // compact: structural nonzeros, then a zero
   L.Bm = o; o += (N - 1) * NX * nu;
   L.Bp = o; o += (N - 1) * NX * nu;
   L.w = o; o += (N - 1) * NX;

@@ -57,10 +57,12 @@ using namespace pdg;
 // The persistent kernel of form 3 (FP32) is built for at most
 // PDG_KS_PERS_MAXT threads (N <= 32 needs 256), so that it may take 65536 /
 // PDG_KS_PERS_MAXT registers (168 for 384 threads: three CTAs per SM at N =
-// 15; at 128 registers its PIPG loop reloads its tiles from local memory).  It also inlines the discretization (PDG_KS_DISC_INLINE):
-// an out-of-line call costs its PIPG loop registers.
+// 15; at 128 registers its PIPG loop reloads its tiles from local memory).
+// PDG_KS_DISC_INLINE=1 inlines the discretization into that kernel instead
+// of calling it (the call costs the PIPG loop registers, the inlined body
+// spills in turn; measured slower with the pipelined discretization).
 #ifndef PDG_KS_DISC_INLINE
-#define PDG_KS_DISC_INLINE 1
+#define PDG_KS_DISC_INLINE 0
 #endif
 #ifndef PDG_KS_PERS_MAXT
 #define PDG_KS_PERS_MAXT 384
@@ -468,7 +470,10 @@ k_subproblem(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
   __syncthreads();
   phase_discretize<R, NU>(P, L, sm);
   __syncthreads();
-  for (int t = threadIdx.x; t < (Nmax - 1) * NX * NX; t += blockDim.x) Am[oA + t] = t < (N - 1) * NX * NX ? double(sm[L.Am + t]) : 0.0;
+  for (int t = threadIdx.x; t < (Nmax - 1) * NX * NX; t += blockDim.x) {  // compact block -> dense
+    const int k = t / (NX * NX), rc = t - k * NX * NX, r = rc / NX, c = rc - r * NX;
+    Am[oA + t] = k < N - 1 ? double(sm[L.Am + k * STM_SAS + stm_index(r, c)]) : 0.0;
+  }
   for (int t = threadIdx.x; t < (Nmax - 1) * NX * NU; t += blockDim.x) {
     Bm[oB + t] = t < (N - 1) * NX * NU ? double(sm[L.Bm + t]) : 0.0;
     Bp[oB + t] = t < (N - 1) * NX * NU ? double(sm[L.Bp + t]) : 0.0;
@@ -916,15 +921,23 @@ static bool fill_dparams(const pdg_params* p, DParams* d, std::string* why) {
 }
 
 
-// Threads per CTA for instances of N nodes: one thread per dual row (whole
-// warps) plus the warp of CTCS rows; in FP64, when three CTAs fit on an SM by
-// shared memory, half of that (more CTAs per SM keep the FP64 pipe busier).
-// Within [128, 512].
+// Threads per CTA for instances of N nodes.  FP32: one thread per dual row
+// (whole warps) plus the warp of CTCS rows.  FP64: as many CTAs per SM as
+// shared memory holds (at most four; more keep the FP64 pipe busier), each
+// with the threads that the kernels' 128 registers per thread leave for that
+// many (128, 160, 256 or 512), but no more than the FP32 count.  Within
+// [128, 512].
 static int threads_for(int N, int nu, int precision) {
-  int t = round32((N - 1) * NX) + 32;
+  const int full = round32((N - 1) * NX) + 32;
+  int t = full;
   if (precision == 0) {
-    const Lay L = make_lay(N, nu, t);
-    if ((size_t)L.total * 8 * 3 <= 227 * 1024) t = round32(round32((N - 1) * NX) / 2) + 32;
+    for (int c = 4; c >= 1; --c) {
+      int tc = (65536 / (128 * c)) & ~31;
+      if (tc > full) tc = full;
+      if (tc < 128) tc = 128;
+      const Lay L = make_lay(N, nu, tc);
+      if (L.ipw >= 1 && (size_t)c * ((size_t)L.total * 8 + 1024) <= 228 * 1024) { t = tc; break; }
+    }
   }
   if (t > 512) t = 512;
   if (t < 128) t = 128;

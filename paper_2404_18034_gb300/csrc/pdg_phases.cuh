@@ -53,69 +53,93 @@ __device__ __forceinline__ R discretize_body(const DParams& P, const Lay& L, R* 
   const int cu = c >= NX ? (c - NX) % NU : -1;
   const bool minus = c >= NX && (c - NX) < NU;
   R dmax = 0;
+  constexpr int JS = SA_A + NX * NU;  // one Jacobian buffer: compact df/dx, dense df/du
+  const int S = 4 * nsub;              // RK4 stages of the interval
   for (int k0 = 0; k0 < N - 1; k0 += L.ipw) {
     const int k = k0 + il;
     const bool active = il < L.ipw && k < N - 1;
+    // two Jacobian buffers, then the evaluator's RK4 state of x
     R* st = sm + L.stage + (active ? il : 0) * L.sa;
-    R* xP = st + SA_A + NX * NU;
+    R* xP = st + 2 * JS;
     R* xA = xP + NX;
     R* xS = xA + NX;
     R Pv[NX], Sv[NX], Ac[NX];
+    // stage s = 4 n + g of substep n: its time along the interval
+    auto stage_t = [&](int s) {
+      const int n = s >> 2, g = s & 3;
+      return (R(n) + (g == 0 ? R(0) : (g == 3 ? R(1) : R(0.5)))) / R(nsub);
+    };
+    // the evaluator: f and the Jacobians at stage s into buffer s % 2, then
+    // the RK4 update of x
+    auto eval_stage = [&](int s) {
+      const int g = s & 3;
+      const R lp = stage_t(s);
+      R* J = st + (s & 1) * JS;
+      R u[NU], x[NX], d[NX];
+#pragma unroll
+      for (int i = 0; i < NU; ++i) u[i] = (R(1) - lp) * Ub[k * NU + i] + lp * Ub[(k + 1) * NU + i];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) x[i] = xS[i];
+      model_eval<R, NU>(P, x, u, d, J, J + SA_A);
+      if (g == 0) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { xA[i] = d[i]; xS[i] = xP[i] + h2 * d[i]; }
+      } else if (g == 1) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { xA[i] = fma(R(2), d[i], xA[i]); xS[i] = xP[i] + h2 * d[i]; }
+      } else if (g == 2) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { xA[i] = fma(R(2), d[i], xA[i]); xS[i] = xP[i] + h * d[i]; }
+      } else {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { const R v = xP[i] + h6 * (xA[i] + d[i]); xP[i] = v; xS[i] = v; }
+      }
+    };
+    // a column thread: the STM column's RK4 stage s with the Jacobians of
+    // buffer s % 2
+    auto jvp_stage = [&](int s) {
+      const int g = s & 3;
+      const R lp = stage_t(s);
+      const R* J = st + (s & 1) * JS;
+      R d[NX];
+      const R lam = minus ? (R(1) - lp) : lp;
+      model_jvp<R, NU>(J, J + SA_A, Sv, cu, lam, d);
+      if (g == 0) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { Ac[i] = d[i]; Sv[i] = Pv[i] + h2 * d[i]; }
+      } else if (g == 1) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { Ac[i] = fma(R(2), d[i], Ac[i]); Sv[i] = Pv[i] + h2 * d[i]; }
+      } else if (g == 2) {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { Ac[i] = fma(R(2), d[i], Ac[i]); Sv[i] = Pv[i] + h * d[i]; }
+      } else {
+#pragma unroll
+        for (int i = 0; i < NX; ++i) { Pv[i] += h6 * (Ac[i] + d[i]); Sv[i] = Pv[i]; }
+      }
+    };
     if (active) {
       if (evaluator) {
 #pragma unroll
         for (int i = 0; i < NX; ++i) { xP[i] = Xb[k * NX + i]; xS[i] = Xb[k * NX + i]; }
+        eval_stage(0);
       } else {
 #pragma unroll
         for (int i = 0; i < NX; ++i) { Pv[i] = (c == i) ? R(1) : R(0); Sv[i] = Pv[i]; }
       }
     }
-    for (int n = 0; n < nsub; ++n) {
+    __syncthreads();
+    // software pipeline: while the column threads take stage s, the
+    // evaluator warp already evaluates stage s + 1 into the other buffer (it
+    // needs only its own x), so a stage costs one barrier and the longer of
+    // the two instead of both in turn
 #pragma unroll 1
-      for (int sgi = 0; sgi < 4; ++sgi) {
-        const R lp = (R(n) + (sgi == 0 ? R(0) : (sgi == 3 ? R(1) : R(0.5)))) / R(nsub);
-        if (active && evaluator) {
-          R u[NU], x[NX], d[NX];
-#pragma unroll
-          for (int i = 0; i < NU; ++i) u[i] = (R(1) - lp) * Ub[k * NU + i] + lp * Ub[(k + 1) * NU + i];
-#pragma unroll
-          for (int i = 0; i < NX; ++i) x[i] = xS[i];
-          model_eval<R, NU>(P, x, u, d, st, st + SA_A);
-          if (sgi == 0) {
-#pragma unroll
-            for (int i = 0; i < NX; ++i) { xA[i] = d[i]; xS[i] = xP[i] + h2 * d[i]; }
-          } else if (sgi == 1) {
-#pragma unroll
-            for (int i = 0; i < NX; ++i) { xA[i] = fma(R(2), d[i], xA[i]); xS[i] = xP[i] + h2 * d[i]; }
-          } else if (sgi == 2) {
-#pragma unroll
-            for (int i = 0; i < NX; ++i) { xA[i] = fma(R(2), d[i], xA[i]); xS[i] = xP[i] + h * d[i]; }
-          } else {
-#pragma unroll
-            for (int i = 0; i < NX; ++i) { const R v = xP[i] + h6 * (xA[i] + d[i]); xP[i] = v; xS[i] = v; }
-          }
-        }
-        __syncthreads();
-        if (active && !evaluator) {
-          R d[NX];
-          const R lam = minus ? (R(1) - lp) : lp;
-          model_jvp<R, NU>(st, st + SA_A, Sv, cu, lam, d);
-          if (sgi == 0) {
-#pragma unroll
-            for (int i = 0; i < NX; ++i) { Ac[i] = d[i]; Sv[i] = Pv[i] + h2 * d[i]; }
-          } else if (sgi == 1) {
-#pragma unroll
-            for (int i = 0; i < NX; ++i) { Ac[i] = fma(R(2), d[i], Ac[i]); Sv[i] = Pv[i] + h2 * d[i]; }
-          } else if (sgi == 2) {
-#pragma unroll
-            for (int i = 0; i < NX; ++i) { Ac[i] = fma(R(2), d[i], Ac[i]); Sv[i] = Pv[i] + h * d[i]; }
-          } else {
-#pragma unroll
-            for (int i = 0; i < NX; ++i) { Pv[i] += h6 * (Ac[i] + d[i]); Sv[i] = Pv[i]; }
-          }
-        }
-        __syncthreads();
+    for (int s = 0; s < S; ++s) {
+      if (active) {
+        if (!evaluator) jvp_stage(s);
+        else if (s + 1 < S) eval_stage(s + 1);
       }
+      __syncthreads();
     }
     if (active) {
       if (evaluator) {
@@ -128,7 +152,10 @@ __device__ __forceinline__ R discretize_body(const DParams& P, const Lay& L, R* 
       } else if (c < NX) {
         const R pc = R(P.Px[c]);
 #pragma unroll
-        for (int i = 0; i < NX; ++i) Am[(k * NX + i) * NX + c] = Pv[i] * pc * R(P.Pxinv[i]);
+        for (int i = 0; i < NX; ++i)
+          if (stm_nz(i, c)) Am[k * STM_SAS + stm_index(i, c)] = Pv[i] * pc * R(P.Pxinv[i]);
+        if (c == 0)  // the block's zero and padding
+          for (int q = kStm.nnz; q < STM_SAS; ++q) Am[k * STM_SAS + q] = R(0);
       } else {
         const R pc = R(P.Pu[cu]);
         R* Bt = minus ? Bm : Bp;
@@ -142,9 +169,8 @@ __device__ __forceinline__ R discretize_body(const DParams& P, const Lay& L, R* 
   block_max_k<R, 1>(v, sm + L.red);
   return v[0];
 }
-// Out of line by default (one copy serves every kernel).  The persistent
-// kernel of PIPG form 3 inlines the body instead: a call in that kernel
-// leaves its PIPG loop fewer registers for its tiles.
+// Out of line (one copy serves every kernel); the persistent kernel of PIPG
+// form 3 can inline the body instead (PDG_KS_DISC_INLINE).
 template <typename R, int NU>
 __device__ PDG_DISC_ATTR R phase_discretize(const DParams& P, const Lay& L, R* sm) {
   return discretize_body<R, NU>(P, L, sm);
@@ -235,15 +261,15 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
           const int rr = t / (N - 1);
           const int k = t - rr * (N - 1), i = kStm.row_order[rr];
           const int o = k * NX + i;
-          const R* a = Am + (k * NX + i) * NX;
+          const R* a = Am + k * STM_SAS;
           const R* xk = px + k * NX;
           R r = pp[o] - pn[o] - px[(k + 1) * NX + i];
           const int nj = kStm.row_nnz[kStm.row_order[(t & ~31) / (N - 1)]];
-          const unsigned long long lst = kStm.row_list[i];
+          const unsigned long long lst = kStm.row_list[i], w0 = kStm.row_off[i][0], w1 = kStm.row_off[i][1];
 #pragma unroll 5
           for (int j = 0; j < nj; ++j) {
             const int cc = int(lst >> (4 * j)) & 15;
-            r += a[cc] * xk[cc];
+            r += a[stm_off(w0, w1, j)] * xk[cc];
           }
           const R* bm = Bm + (k * NX + i) * NU;
           const R* bp = Bp + (k * NX + i) * NU;
@@ -271,14 +297,14 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
           const bool hasA = k < N - 1, hasP = k > 0;
           const int ka = hasA ? k : 0, kp = hasP ? k - 1 : 0;
           R gc = 0;
-          const R* a = Am + ka * NX * NX + i;
+          const R* a = Am + ka * STM_SAS;
           const R* f = ph + ka * NX;
           const int nj = kStm.col_nnz[kStm.col_order[(t & ~31) / N]];
-          const unsigned long long lst = kStm.col_list[i];
+          const unsigned long long lst = kStm.col_list[i], w0 = kStm.col_off[i][0], w1 = kStm.col_off[i][1];
 #pragma unroll 5
           for (int j = 0; j < nj; ++j) {
             const int r = int(lst >> (4 * j)) & 15;
-            gc = fma(a[r * NX], f[r], gc);
+            gc = fma(a[stm_off(w0, w1, j)], f[r], gc);
           }
           R g = hasA ? gc : R(0);
           const R dth = (hasP ? pt[kp] : R(0)) - (hasA ? pt[ka] : R(0));
@@ -437,14 +463,14 @@ __device__ PDG_PIPG_ATTR int phase_pipg(const DParams& P, const Lay& L, R* sm, R
           const R xv = xt[o];
           const R G0 = fma(i == IY ? R(1) : R(0), td[k], -vph[(k - 1) * NX + i]);
           R Gc = G0;
-          const R* a = Am + km * NX * NX + i;
+          const R* a = Am + km * STM_SAS;
           const R* f = vph + km * NX;
           const int nj = kStm.col_nnz[kStm.col_order[(t & ~31) / (N - 1)]];
-          const unsigned long long lst = kStm.col_list[i];
+          const unsigned long long lst = kStm.col_list[i], w0 = kStm.col_off[i][0], w1 = kStm.col_off[i][1];
 #pragma unroll 5
           for (int j = 0; j < nj; ++j) {
             const int r = int(lst >> (4 * j)) & 15;
-            Gc = fma(a[r * NX], f[r], Gc);
+            Gc = fma(a[stm_off(w0, w1, j)], f[r], Gc);
           }
           const R G = last ? G0 : Gc;
           // e_cost = -e_m on x_N (maximize m_N) folded into the same FMA
@@ -559,15 +585,15 @@ __device__ PDG_PIPG_ATTR int phase_pipg(const DParams& P, const Lay& L, R* sm, R
           }
           mup[o] = mp;
           mum[o] = mm;
-          const R* a_ = Am + (k * NX + i) * NX;
+          const R* a_ = Am + k * STM_SAS;
           const R* d = dx + k * NX;
           R r = wv[o] + (fma(R(2), mp, -a) - fma(R(2), mm, -b)) - dx[(k + 1) * NX + i];
           const int nj = kStm.row_nnz[kStm.row_order[(t & ~31) / (N - 1)]];
-          const unsigned long long lst = kStm.row_list[i];
+          const unsigned long long lst = kStm.row_list[i], w0 = kStm.row_off[i][0], w1 = kStm.row_off[i][1];
 #pragma unroll 5
           for (int j = 0; j < nj; ++j) {
             const int cc = int(lst >> (4 * j)) & 15;
-            r += a_[cc] * d[cc];
+            r += a_[stm_off(w0, w1, j)] * d[cc];
           }
           const R* bm = Bm + (k * NX + i) * NU;
           const R* bp = Bp + (k * NX + i) * NU;
@@ -778,10 +804,10 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
     r0 = r1 = sm[L.xh + kx * NX + i];
     if (has_colA) {
 #pragma unroll
-      for (int r = 0; r < NX; ++r) a1[r] = sm[L.Am + (kx * NX + r) * NX + i];
+      for (int r = 0; r < NX; ++r) a1[r] = sm[L.Am + kx * STM_SAS + stm_index(r, i)];
     }
 #pragma unroll
-    for (int c = 0; c < NX; ++c) a2[c] = sm[L.Am + (kd * NX + i) * NX + c];
+    for (int c = 0; c < NX; ++c) a2[c] = sm[L.Am + kd * STM_SAS + stm_index(i, c)];
 #pragma unroll
     for (int c = 0; c < NU; ++c) {
       a3[c] = sm[L.Bm + (kd * NX + i) * NU + c];
@@ -1142,8 +1168,8 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
     for (int q = 0; q < TC; ++q) {
       const int c = TC * cb + (q ^ pcol);
       const bool okc = has_iv && c < NX;
-      ap[h][q] = PR::mk((okc && r0 < NX) ? sm[L.Am + (g * NX + r0) * NX + c] : R(0),
-                        (okc && r1 < NX) ? sm[L.Am + (g * NX + r1) * NX + c] : R(0));
+      ap[h][q] = PR::mk((okc && r0 < NX) ? sm[L.Am + g * STM_SAS + stm_index(r0, c)] : R(0),
+                        (okc && r1 < NX) ? sm[L.Am + g * STM_SAS + stm_index(r1, c)] : R(0));
     }
 #pragma unroll
     for (int s = 0; s < NC; ++s) {

@@ -28,7 +28,7 @@ def _probe(tmp_path, defs):
     out = subprocess.run([exe], capture_output=True, text=True, timeout=60, check=True).stdout.split("\n")
     nx = int(out[0].split()[1])
     mask = np.zeros((nx, nx), bool)
-    order = []
+    order, offs, compact = [], [], None
     for line in out[1:]:
         f = line.split()
         if f and f[0] == "mask":
@@ -36,7 +36,11 @@ def _probe(tmp_path, defs):
             mask[i] = [(m >> c) & 1 for c in range(nx)]
         elif f and f[0] == "order":  # a, row_order[a], col_order[a], nnz of row a, of column a, their lists
             order.append([int(v) for v in f[2:]])
-    return mask, order
+        elif f and f[0] == "compact":
+            compact = (int(f[1]), int(f[2]))
+        elif f and f[0] == "offsets":  # a, row_start[a], row_off[a][0..1], col_off[a][0..1]
+            offs.append([int(v) for v in f[2:]])
+    return mask, order, compact, offs
 
 
 def _sampled_pattern(O, inputs, model, nx, trials=24):
@@ -60,7 +64,7 @@ def _sampled_pattern(O, inputs, model, nx, trials=24):
 
 @pytest.mark.parametrize("model,defs", [("6dof", []), ("3dof", ["-DPDG_MODEL_3DOF"])])
 def test_declared_stm_sparsity_matches_oracle(tmp_path, oracle, inputs, model, defs):
-    mask, order = _probe(tmp_path, defs)
+    mask, order, compact, offs = _probe(tmp_path, defs)
     nx = mask.shape[0]
     seen = _sampled_pattern(oracle, inputs, model, nx)
     assert not np.any(seen & ~mask), np.argwhere(seen & ~mask)   # nothing nonzero outside the mask
@@ -82,3 +86,18 @@ def test_declared_stm_sparsity_matches_oracle(tmp_path, oracle, inputs, model, d
         assert order[i][2] == rn[i] and order[i][3] == cn[i]
         assert ridx[:rn[i]] == list(np.nonzero(mask[i])[0]) and all(not mask[i, c] for c in ridx[rn[i]:])
         assert cidx[:cn[i]] == list(np.nonzero(mask[:, i])[0]) and all(not mask[r, i] for r in cidx[cn[i]:])
+    # compact storage: interval k keeps its nonzeros row by row, columns
+    # ascending, then a zero, padded to an odd count; every list entry's
+    # offset names that nonzero, and every padding entry the zero
+    nnz, sas = compact
+    assert nnz == int(mask.sum()) and sas == (nnz + 1) | 1
+    pos = -np.ones((nx, nx), int)
+    pos[mask] = np.arange(nnz)                       # row-major order of the nonzeros
+    for i in range(nx):
+        rs, r0, r1, c0, c1 = offs[i]
+        ro = [((r0 if j < 8 else r1) >> (8 * (j % 8))) & 255 for j in range(nx)]
+        co = [((c0 if j < 8 else c1) >> (8 * (j % 8))) & 255 for j in range(nx)]
+        nz_c, nz_r = np.nonzero(mask[i])[0], np.nonzero(mask[:, i])[0]
+        assert rs == (pos[i, nz_c[0]] if len(nz_c) else rs)
+        assert ro[:len(nz_c)] == [pos[i, c] for c in nz_c] and all(o == nnz for o in ro[len(nz_c):])
+        assert co[:len(nz_r)] == [pos[r, i] for r in nz_r] and all(o == nnz for o in co[len(nz_r):])
