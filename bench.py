@@ -36,11 +36,11 @@ METRIC = "converged PDG SCP solves/s on 1 GB300, batch 16384, N=15; % FP64/FP32 
 # kernel per instance, from ncu captures of the kernel sources with the given
 # hash (profiles/ has the summaries); reported only while the sources match.
 PROFILED_TRAFFIC = {
-    # ncu (dram__bytes_read.sum, dram__bytes_write.sum) of k_persistent<double,4,1>:
-    # 6-DoF on 456 instances (one per CTA slot), 12.03 MB read + 71.16 MB written;
-    # 3-DoF on 608 instances at its tuned 128 threads, 3.056 MB read + 0.066 MB written
-    "3dc399354509043f": {("6dof", "fp64", 4, 15, "persistent"): 83.19e6 / 456,
-                         ("3dof", "fp64", 4, 15, "persistent"): 3.122e6 / 608},
+    # ncu (dram__bytes_read.sum, dram__bytes_write.sum) of k_persistent<double,4,1> at
+    # its tuned 128 threads, 608 instances (one per CTA slot, four per SM):
+    # 6-DoF 14.46 MB read + 174.14 MB written; 3-DoF 3.043 MB read + 0.038 MB written
+    "c994b5741c3704dc": {("6dof", "fp64", 4, 15, "persistent"): 188.59e6 / 608,
+                         ("3dof", "fp64", 4, 15, "persistent"): 3.082e6 / 608},
 }
 
 

@@ -95,7 +95,7 @@ def _fitting(ts: Iterable[int], n_max: int, nu: int, precision: int, model: str 
             continue
         n = n_max
         sas = (NNZA[model] + 1) | 1  # compact hat A^-: nonzeros, a zero, odd count
-        img = 8 + 16 + n * NX + n * nu + (n - 1) * (sas + 2 * NX * nu + NX + 1) + 2 * n + 2 * NX + \
+        img = 8 + 16 + n * NX + n * nu + (n - 1) * (sas + 2 * ((NX * nu) | 1) + NX + 1) + 2 * n + 2 * NX + \
             n * NX + n * nu + 3 * (n - 1) * NX + (n - 1)
         uni = max(2 * n * NX + 2 * n * nu + 4 * (n - 1) * NX + (n - 1), ipw * (2 * (sa + NX * nu) + 3 * NX))
         if (img + uni + 210) * esz > SMEM_MAX:

@@ -160,14 +160,14 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
         const double uv = ut[q];
         double Gm = 0;
         {
-          const double* a = Bm + km * NX * NU + cc;
+          const double* a = Bm + km * b_stride(NU) + cc;
           const double* f = vph + km * NX;
           for (int r = 0; r < NX; ++r) Gm = fma(a[r * NU], f[r], Gm);
         }
         Gm = hasM ? Gm : 0.0;
         double Gs = Gm;
         {
-          const double* a = Bp + kp * NX * NU + cc;
+          const double* a = Bp + kp * b_stride(NU) + cc;
           const double* f = vph + kp * NX;
           for (int r = 0; r < NX; ++r) Gs = fma(a[r * NU], f[r], Gs);
         }
@@ -211,7 +211,8 @@ __device__ void grad_pipg_iter(const DParams& P, const Lay& L, const AdjLay& A, 
           r = fma(Am[k * STM_SAS + stm_off(w0, w1, j)], dx[k * NX + c], r);
         }
         for (int c = 0; c < NU; ++c)
-          r = fma(Bp[o * NU + c], du[(k + 1) * NU + c], fma(Bm[o * NU + c], du[k * NU + c], r));
+          r = fma(Bp[k * b_stride(NU) + i * NU + c], du[(k + 1) * NU + c],
+                  fma(Bm[k * b_stride(NU) + i * NU + c], du[k * NU + c], r));
         sm[L.mup + o] = mp;
         sm[L.mum + o] = mm;
         sm[L.phi + o] = fma(beta, r, f);
@@ -340,10 +341,10 @@ __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& 
         const bool hasM = k < N - 1, hasP = k > 0;
         const int km = hasM ? k : 0, kp = hasP ? k - 1 : 0;
         double dm = 0;
-        for (int r = 0; r < NX; ++r) dm = fma(Bm[(km * NX + r) * NU + cc], rb[km * NX + r], dm);
+        for (int r = 0; r < NX; ++r) dm = fma(Bm[km * b_stride(NU) + r * NU + cc], rb[km * NX + r], dm);
         dm = hasM ? dm : 0.0;
         double dp = dm;
-        for (int r = 0; r < NX; ++r) dp = fma(Bp[(kp * NX + r) * NU + cc], rb[kp * NX + r], dp);
+        for (int r = 0; r < NX; ++r) dp = fma(Bp[kp * b_stride(NU) + r * NU + cc], rb[kp * NX + r], dp);
         const double d = hasP ? dp : dm;
         const double uhb = fma(2.0, d, fma(rho, utb[q], last ? sm[A.uob + q] : 0.0));
         // the mask is 0.0 or 1.0: test its bit pattern, not on the FP64 pipe
@@ -374,7 +375,8 @@ __device__ void grad_pipg_reverse(const DParams& P, const Lay& L, const AdjLay& 
         fb = k >= 1 ? fa : fb;
         fb -= Gb[(k + 1) * NX + i];
         for (int c = 0; c < NU; ++c)
-          fb = fma(Bp[o * NU + c], Gub[(k + 1) * NU + c], fma(Bm[o * NU + c], Gub[k * NU + c], fb));
+          fb = fma(Bp[k * b_stride(NU) + i * NU + c], Gub[(k + 1) * NU + c],
+                   fma(Bm[k * b_stride(NU) + i * NU + c], Gub[k * NU + c], fb));
         vphb[o] = fb;
         if (k == 0) {  // interval 1: cotangents of hat B^-_1, hat B^+_1 (row i)
           const double ph = vph[o];

@@ -213,6 +213,11 @@ __host__ __device__ inline int waves_ipw(int threads, int nu) {
 
 __host__ __device__ inline int round32(int x) { return (x + 31) & ~31; }
 
+// Elements per interval of hat B^- and hat B^+ (row-major NX x nu): odd, so
+// that the same entry of consecutive intervals (the tasks of a warp) falls in
+// different shared-memory banks.
+__host__ __device__ constexpr int b_stride(int nu) { return (NX * nu) | 1; }
+
 __host__ __device__ inline Lay make_lay(int N, int nu, int threads) {
   Lay L;
   L.N = N;
@@ -225,8 +230,8 @@ __host__ __device__ inline Lay make_lay(int N, int nu, int threads) {
   L.Xb = o; o += N * NX;
   L.Ub = o; o += N * nu;
   L.Am = o; o += (N - 1) * STM_SAS;  // compact: structural nonzeros, then a zero
-  L.Bm = o; o += (N - 1) * NX * nu;
-  L.Bp = o; o += (N - 1) * NX * nu;
+  L.Bm = o; o += (N - 1) * b_stride(nu);
+  L.Bp = o; o += (N - 1) * b_stride(nu);
   L.w = o; o += (N - 1) * NX;
   L.eps = o; o += N - 1;
   L.lo = o; o += N;

@@ -474,9 +474,10 @@ k_subproblem(const DParams P, int B, int Nmax, const double* __restrict__ x0, co
     const int k = t / (NX * NX), rc = t - k * NX * NX, r = rc / NX, c = rc - r * NX;
     Am[oA + t] = k < N - 1 ? double(sm[L.Am + k * STM_SAS + stm_index(r, c)]) : 0.0;
   }
-  for (int t = threadIdx.x; t < (Nmax - 1) * NX * NU; t += blockDim.x) {
-    Bm[oB + t] = t < (N - 1) * NX * NU ? double(sm[L.Bm + t]) : 0.0;
-    Bp[oB + t] = t < (N - 1) * NX * NU ? double(sm[L.Bp + t]) : 0.0;
+  for (int t = threadIdx.x; t < (Nmax - 1) * NX * NU; t += blockDim.x) {  // strided blocks -> dense
+    const int k = t / (NX * NU), o = k * b_stride(NU) + (t - k * NX * NU);
+    Bm[oB + t] = k < N - 1 ? double(sm[L.Bm + o]) : 0.0;
+    Bp[oB + t] = k < N - 1 ? double(sm[L.Bp + o]) : 0.0;
   }
   for (int t = threadIdx.x; t < (Nmax - 1) * NX; t += blockDim.x) w[ow + t] = t < (N - 1) * NX ? double(sm[L.w + t]) : 0.0;
 }

@@ -160,7 +160,7 @@ __device__ __forceinline__ R discretize_body(const DParams& P, const Lay& L, R* 
         const R pc = R(P.Pu[cu]);
         R* Bt = minus ? Bm : Bp;
 #pragma unroll
-        for (int i = 0; i < NX; ++i) Bt[(k * NX + i) * NU + cu] = Pv[i] * pc * R(P.Pxinv[i]);
+        for (int i = 0; i < NX; ++i) Bt[k * b_stride(NU) + i * NU + cu] = Pv[i] * pc * R(P.Pxinv[i]);
       }
     }
     __syncthreads();
@@ -271,8 +271,8 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
             const int cc = int(lst >> (4 * j)) & 15;
             r += a[stm_off(w0, w1, j)] * xk[cc];
           }
-          const R* bm = Bm + (k * NX + i) * NU;
-          const R* bp = Bp + (k * NX + i) * NU;
+          const R* bm = Bm + k * b_stride(NU) + i * NU;
+          const R* bp = Bp + k * b_stride(NU) + i * NU;
 #pragma unroll
           for (int cc = 0; cc < NU; ++cc) r += bm[cc] * pu[k * NU + cc] + bp[cc] * pu[(k + 1) * NU + cc];
           ph[o] = r * isig;
@@ -321,7 +321,7 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
           const int km = hasM ? k : 0, kp = hasP ? k - 1 : 0;
           R gm = 0;
           {
-            const R* a = Bm + km * NX * NU + cc;
+            const R* a = Bm + km * b_stride(NU) + cc;
             const R* f = ph + km * NX;
 #pragma unroll
             for (int r = 0; r < NX; ++r) gm = fma(a[r * NU], f[r], gm);
@@ -329,7 +329,7 @@ __device__ R phase_power(const DParams& P, const Lay& L, R* sm, int force, int* 
           gm = hasM ? gm : R(0);
           R g = gm;
           {
-            const R* a = Bp + kp * NX * NU + cc;
+            const R* a = Bp + kp * b_stride(NU) + cc;
             const R* f = ph + kp * NX;
 #pragma unroll
             for (int r = 0; r < NX; ++r) g = fma(a[r * NU], f[r], g);
@@ -500,7 +500,7 @@ __device__ PDG_PIPG_ATTR int phase_pipg(const DParams& P, const Lay& L, R* sm, R
           const R uv = ut[kv * NU + cv];
           R Gm = 0;
           {
-            const R* a = Bm + km * NX * NU + cv;
+            const R* a = Bm + km * b_stride(NU) + cv;
             const R* f = vph + km * NX;
 #pragma unroll
             for (int r = 0; r < NX; ++r) Gm = fma(a[r * NU], f[r], Gm);
@@ -508,7 +508,7 @@ __device__ PDG_PIPG_ATTR int phase_pipg(const DParams& P, const Lay& L, R* sm, R
           Gm = kv < N - 1 ? Gm : R(0);
           R Gs = Gm;
           {
-            const R* a = Bp + kp * NX * NU + cv;
+            const R* a = Bp + kp * b_stride(NU) + cv;
             const R* f = vph + kp * NX;
 #pragma unroll
             for (int r = 0; r < NX; ++r) Gs = fma(a[r * NU], f[r], Gs);
@@ -595,8 +595,8 @@ __device__ PDG_PIPG_ATTR int phase_pipg(const DParams& P, const Lay& L, R* sm, R
             const int cc = int(lst >> (4 * j)) & 15;
             r += a_[stm_off(w0, w1, j)] * d[cc];
           }
-          const R* bm = Bm + (k * NX + i) * NU;
-          const R* bp = Bp + (k * NX + i) * NU;
+          const R* bm = Bm + k * b_stride(NU) + i * NU;
+          const R* bp = Bp + k * b_stride(NU) + i * NU;
 #pragma unroll
           for (int cc = 0; cc < NU; ++cc) { r += bm[cc] * du[k * NU + cc]; r += bp[cc] * du[(k + 1) * NU + cc]; }
           const R pn = f + beta * r;
@@ -810,8 +810,8 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
     for (int c = 0; c < NX; ++c) a2[c] = sm[L.Am + kd * STM_SAS + stm_index(i, c)];
 #pragma unroll
     for (int c = 0; c < NU; ++c) {
-      a3[c] = sm[L.Bm + (kd * NX + i) * NU + c];
-      a3[NU + c] = sm[L.Bp + (kd * NX + i) * NU + c];
+      a3[c] = sm[L.Bm + kd * b_stride(NU) + i * NU + c];
+      a3[NU + c] = sm[L.Bp + kd * b_stride(NU) + i * NU + c];
     }
     r8 = sm[L.w + tid];
     r4 = sm[L.mup + tid]; r2 = r4 - aw;
@@ -823,11 +823,11 @@ __device__ PDG_PREG_ATTR int phase_pipg_reg(const DParams& P, const Lay& L, R* /
     r0 = r1 = sm[L.uh + ku * NU + cc];
     if (ku <= N - 2) {
 #pragma unroll
-      for (int r = 0; r < NX; ++r) a1[r] = sm[L.Bm + (ku * NX + r) * NU + cc];
+      for (int r = 0; r < NX; ++r) a1[r] = sm[L.Bm + ku * b_stride(NU) + r * NU + cc];
     }
     if (ku >= 1) {
 #pragma unroll
-      for (int r = 0; r < NX; ++r) a2[r] = sm[L.Bp + ((ku - 1) * NX + r) * NU + cc];
+      for (int r = 0; r < NX; ++r) a2[r] = sm[L.Bp + (ku - 1) * b_stride(NU) + r * NU + cc];
     }
     if (cc == NU - 1) { r2 = sm[L.lo + ku]; r3 = sm[L.hi + ku]; }
     if (cc < 3) r4 = sm[L.Ub + ku * NU + cc];
@@ -1175,10 +1175,10 @@ __device__ PDG_PKS_ATTR int phase_pipg_ks(const DParams& P, const Lay& L, R* /*i
     for (int s = 0; s < NC; ++s) {
       const int cc = cb + NCB * s;
       const bool okc = has_iv && cc < NU;
-      bm[h][s] = PR::mk((okc && r0 < NX) ? sm[L.Bm + (g * NX + r0) * NU + cc] : R(0),
-                        (okc && r1 < NX) ? sm[L.Bm + (g * NX + r1) * NU + cc] : R(0));
-      bp[h][s] = PR::mk((okc && r0 < NX) ? sm[L.Bp + (g * NX + r0) * NU + cc] : R(0),
-                        (okc && r1 < NX) ? sm[L.Bp + (g * NX + r1) * NU + cc] : R(0));
+      bm[h][s] = PR::mk((okc && r0 < NX) ? sm[L.Bm + g * b_stride(NU) + r0 * NU + cc] : R(0),
+                        (okc && r1 < NX) ? sm[L.Bm + g * b_stride(NU) + r1 * NU + cc] : R(0));
+      bp[h][s] = PR::mk((okc && r0 < NX) ? sm[L.Bp + g * b_stride(NU) + r0 * NU + cc] : R(0),
+                        (okc && r1 < NX) ? sm[L.Bp + g * b_stride(NU) + r1 * NU + cc] : R(0));
     }
   }
   // ---- iterates.  x components TC cb + WC rb + e of node g, dual rows

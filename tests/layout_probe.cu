@@ -32,9 +32,10 @@ int main() {
         // image regions, in order, each as large as the kernels index it
         CHECK(NX - 1 <= 16, N, nu, T);  // x0 slots
         CHECK(L.x0 + 16 <= L.Xb && L.Xb + N * NX <= L.Ub && L.Ub + N * nu <= L.Am, N, nu, T);
-        CHECK(L.Am + (N - 1) * STM_SAS <= L.Bm && L.Bm + (N - 1) * NX * nu <= L.Bp, N, nu, T);
+        CHECK(L.Am + (N - 1) * STM_SAS <= L.Bm && L.Bm + (N - 1) * b_stride(nu) <= L.Bp, N, nu, T);
+        CHECK(b_stride(nu) >= NX * nu && b_stride(nu) % 2 == 1, N, nu, T);
         CHECK(STM_SAS > make_stm_order().nnz && STM_SAS % 2 == 1 && make_stm_order().nnz <= NX * NX, N, nu, T);
-        CHECK(L.Bp + (N - 1) * NX * nu <= L.w && L.w + (N - 1) * NX <= L.eps, N, nu, T);
+        CHECK(L.Bp + (N - 1) * b_stride(nu) <= L.w && L.w + (N - 1) * NX <= L.eps, N, nu, T);
         CHECK(L.xh + N * NX <= L.uh && L.uh + N * nu <= L.mup && L.th + (N - 1) <= L.img, N, nu, T);
         // the phase-local union: PIPG form 1 and the discretization's stage buffers
         CHECK(L.img <= L.xt && L.td + N <= L.red, N, nu, T);
