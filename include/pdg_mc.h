@@ -282,7 +282,7 @@ int pdg_mc_pipg_form(const pdg_handle* h);
  * lives in a fixed 32 MiB device array that the library defines, so every
  * GPU that loads the library holds those 32 MiB until the process exits (each
  * model library has its own array: a process using both holds 64 MiB).
- *   - Batches that need more than the 32 MiB (about 650 instances at
+ *   - Batches that need more than the 32 MiB (about 870 instances at
  *     n_max = 15 in FP64, twice that in FP32) are rejected with PDG_EINVAL
  *     and a message that states the limit; nothing is launched.
  *   - The first call on a device looks up the array's device address
