@@ -1,7 +1,8 @@
 // layout_probe.cu -- test infrastructure: checks on the host that the
 // per-instance shared-memory layouts of the solver (make_lay, make_reg_lay,
 // make_ks_lay, make_adj) hold every region the kernels index, for every node count,
-// control size and CTA size the library accepts.  Built by
+// control size and CTA size the library accepts, and the index algebra of
+// PIPG form 3's butterfly exchanges.  Built by
 // tests/test_layout.py once per model; prints "OK <cases>" or the failures.
 #include <cstdio>
 
@@ -18,8 +19,61 @@ static int bad = 0;
     }                                                                                             \
   } while (0)
 
+// PIPG form 3's butterflies, lane by lane on the host: with every lane's
+// partial sums stored in the order of ks_perm, rounds that keep the first
+// half of the stored entries and add the partner's second half (as
+// ks_rs_round does) leave lane sel the full sums of entries (n / M) sel ..
+// (n / M) sel + n / M - 1, and the inverse rounds (ks_ag_round) return every
+// entry in the lane's stored order.
+template <int M, int n>
+static void check_butterflies(long* cases) {
+  int v[M][n], st[M][n];
+  for (int l = 0; l < M; ++l)
+    for (int p = 0; p < n; ++p) v[l][p] = 1 + 7 * l + 131 * p + 3 * l * p;
+  for (int l = 0; l < M; ++l)
+    for (int s = 0; s < n; ++s) st[l][s] = v[l][s ^ ks_perm<M, n>(l)];
+  int cur[M][n], len = n;
+  for (int l = 0; l < M; ++l)
+    for (int s = 0; s < n; ++s) cur[l][s] = st[l][s];
+  for (int mask = M / 2; mask >= 1; mask /= 2) {  // reduce rounds, high lane bit first
+    int nxt[M][n];
+    for (int l = 0; l < M; ++l)
+      for (int e = 0; e < len / 2; ++e) nxt[l][e] = cur[l][e] + cur[l ^ mask][len / 2 + e];
+    len /= 2;
+    for (int l = 0; l < M; ++l)
+      for (int e = 0; e < len; ++e) cur[l][e] = nxt[l][e];
+  }
+  for (int l = 0; l < M; ++l)
+    for (int e = 0; e < n / M; ++e) {
+      int want = 0;
+      for (int q = 0; q < M; ++q) want += v[q][(n / M) * l + e];
+      ++*cases;
+      if (cur[l][e] != want) { if (bad < 20) std::printf("FAIL reduce M=%d n=%d lane %d entry %d\n", M, n, l, e); ++bad; }
+    }
+  for (int mask = 1; mask < M; mask *= 2) {  // gather rounds, low lane bit first
+    int nxt[M][n];
+    for (int l = 0; l < M; ++l)
+      for (int e = 0; e < len; ++e) { nxt[l][e] = cur[l][e]; nxt[l][len + e] = cur[l ^ mask][e]; }
+    len *= 2;
+    for (int l = 0; l < M; ++l)
+      for (int e = 0; e < len; ++e) cur[l][e] = nxt[l][e];
+  }
+  for (int l = 0; l < M; ++l)
+    for (int s = 0; s < n; ++s) {
+      int want = 0;
+      for (int q = 0; q < M; ++q) want += v[q][s ^ ks_perm<M, n>(l)];
+      ++*cases;
+      if (cur[l][s] != want) { if (bad < 20) std::printf("FAIL gather M=%d n=%d lane %d entry %d\n", M, n, l, s); ++bad; }
+    }
+}
+
 int main() {
   long cases = 0;
+  check_butterflies<2, 4>(&cases);
+  check_butterflies<2, 8>(&cases);
+  check_butterflies<4, 8>(&cases);
+  check_butterflies<KS_NR, KS_TC>(&cases);
+  check_butterflies<KS_NC, KS_TR>(&cases);
   const int nus[2] = {4, PDG_MODEL_NU_ALT};
   for (int a = 0; a < 2; ++a) {
     const int nu = nus[a];
