@@ -38,9 +38,9 @@ METRIC = "converged PDG SCP solves/s on 1 GB300, batch 16384, N=15; % FP64/FP32 
 PROFILED_TRAFFIC = {
     # ncu (dram__bytes_read.sum, dram__bytes_write.sum) of k_persistent<double,4,1> at
     # its tuned 128 threads, 608 instances (one per CTA slot, four per SM):
-    # 6-DoF 14.32 MB read + 173.22 MB written; 3-DoF 3.146 MB read + 0.036 MB written
-    "7bcdf9d970186bd2": {("6dof", "fp64", 4, 15, "persistent"): 187.54e6 / 608,
-                         ("3dof", "fp64", 4, 15, "persistent"): 3.182e6 / 608},
+    # 6-DoF 14.10 MB read + 171.12 MB written; 3-DoF 3.107 MB read + 0.046 MB written
+    "40b1c3098dc7d69a": {("6dof", "fp64", 4, 15, "persistent"): 185.22e6 / 608,
+                         ("3dof", "fp64", 4, 15, "persistent"): 3.153e6 / 608},
 }
 
 

@@ -262,8 +262,7 @@ int pdg_mc_autotune(pdg_handle* h, int B, const double* x0, const int* n_nodes, 
  *           of 8 (4) lanes holds one interval's blocks and owns one node;
  *           products run as packed pairs and their partial sums combine
  *           by shuffles within the group.  Needs round32(8 N) threads
- *           (round32(4 N) when NX <= 8), at least 64, at most 512 (384 in
- *           FP32);
+ *           (round32(4 N) when NX <= 8), at least 64, at most 512;
  *   form 0: automatic (default) -- form 3 for FP32 when the thread setting
  *           allows it, else form 1.
  * Returns PDG_EINVAL for another value.  Synchronous; no device work. */

@@ -55,9 +55,12 @@ using namespace pdg;
 #define PDG_FP64_MINB 1
 #endif
 // The persistent kernel of form 3 (FP32) is built for at most
-// PDG_KS_PERS_MAXT threads (N <= 32 needs 256), so that it may take 65536 /
-// PDG_KS_PERS_MAXT registers (168 for 384 threads: three CTAs per SM at N =
-// 15; at 128 registers its PIPG loop reloads its tiles from local memory).
+// PDG_KS_PERS_MAXT threads (N <= 32 needs 256) and so takes up to 65536 /
+// PDG_KS_PERS_MAXT registers.  At 512 (128 registers) its PIPG loop reloads
+// some of its tiles from local memory; at 384 (168 registers) it does not,
+// but N = 15 then fits three CTAs per SM instead of four and N = 30 one
+// instead of two: 25 677 against 25 374 solves/s at N = 15, 7461 against
+// 10 553 on the uneven batch, so 512 is the build.
 // PDG_KS_DISC_INLINE=1 inlines the discretization into that kernel instead
 // of calling it (the call costs the PIPG loop registers, the inlined body
 // spills in turn; measured slower with the pipelined discretization).
@@ -65,7 +68,7 @@ using namespace pdg;
 #define PDG_KS_DISC_INLINE 0
 #endif
 #ifndef PDG_KS_PERS_MAXT
-#define PDG_KS_PERS_MAXT 384
+#define PDG_KS_PERS_MAXT 512
 #endif
 #define PDG_LB_PERS(R, PV)                                                                  \
   __launch_bounds__((PV) == 3 && sizeof(R) == 4 ? PDG_KS_PERS_MAXT                            \
